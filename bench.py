@@ -1,0 +1,355 @@
+"""Benchmark: batched FP32 implicitly dealiased 1D complex convolutions.
+
+Workload (the one the headline metric is quoted on): 4096 independent 1D
+complex binary convolutions, m drawn uniformly from the 31 sizes
+{2^k, 3*2^k, 5*2^k} in [64, 65536] (seed 1012), entries uniform[-1, 1],
+complex64, executed as ONE persistent kernel launch replayed from a CUDA
+graph.  A step is one such call over the whole batch.  Reported beside it:
+the plain FP64 path (one launch per instance), parity against the FP64
+oracle on sampled instances, the HBM roofline of the kernel and the CPU
+oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) each rank runs its own batch (weak scaling, no
+collective on the data path) and rank 0 prints the aggregate.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_INST = 4096
+SEED = 1012
+WORKLOAD = ("batched 1D complex binary implicitly dealiased convolution: 4096 instances, "
+            "m uniform over {2^k,3*2^k,5*2^k} in [64,65536], uniform[-1,1] entries, complex64, "
+            "one persistent launch in a CUDA graph")
+METRIC = "dealiased convs/s (FP32 batched, one persistent launch)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank):
+    from paper_1008_1366_gb300 import synthetic
+    ms = synthetic.batched_sizes(N_INST, SEED + 101 * rank)
+    f, g, off = synthetic.batched_inputs(ms, SEED + 7 + 101 * rank)
+    return ms, f, g, off
+
+
+def oracle_convs(ms, f, g, off, budget_s, start=0):
+    """Times the FP64 oracle over instances start, start+1, ... (cyclic) until
+    budget_s seconds of CPU work; returns (convs, seconds, sample text)."""
+    import oracle
+    n = len(ms)
+    t0 = time.perf_counter()
+    done = 0
+    elems = 0
+    while True:
+        i = (start + done) % n
+        a, b = off[i], off[i + 1]
+        oracle.padded_complex(f[a:b], g[a:b])
+        done += 1
+        elems += int(b - a)
+        if time.perf_counter() - t0 >= budget_s or done >= 4 * n:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt, f"{done} instances of the workload in order (sum m = {elems}), numpy FFT, 1 thread"
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1008_1366_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(total_bytes_alg):
+    """DRAM traffic per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("traffic_bytes_per_launch")
+
+
+def measured_peak_hbm():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ms, f, g, off = workload(0)
+    times, convs = [], []
+    cores = 1
+    for s in range(args.warmup + args.steps):
+        n, dt, sample = oracle_convs(ms, f, g, off, budget_s=3.0, start=s * 64)
+        if s >= args.warmup:
+            times.append(dt)
+            convs.append(n)
+    value = sum(convs) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "convs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (bounded sample per step)"},
+        "cpu_baseline": {"value": value, "unit": "convs/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step: about 3 s of " + sample.split(",")[0].split(" (")[0] + " instances"},
+        "e2e": {"value": value, "unit": "convs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    import oracle
+    import paper_1008_1366_gb300 as dcl
+
+    ms, f, g, off = workload(rank)
+    total = int(off[-1])
+    tf = torch.tensor(f, dtype=torch.complex64, device=dev)
+    tg = torch.tensor(g, dtype=torch.complex64, device=dev)
+    th = torch.empty_like(tf)
+    plan = dcl.BatchedPlan(ms, dtype=torch.complex64)
+    work = plan.workspace(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    # parity on sampled instances (outside the timed region)
+    with torch.cuda.stream(stream):
+        plan(tf, tg, out=th, work=work)
+    stream.synchronize()
+    hh = th.cpu().numpy()
+    rng = np.random.default_rng(5)
+    pick = sorted(set(rng.integers(0, len(ms), 24).tolist()) | {int(np.argmax(ms)), int(np.argmin(ms))})
+    worst = 0.0
+    worst_ratio = 0.0
+    for i in pick:
+        a, b = off[i], off[i + 1]
+        ref = oracle.padded_complex(f[a:b], g[a:b])
+        e = float(np.linalg.norm(hh[a:b] - ref) / np.linalg.norm(ref))
+        tol = 5e-7 * np.log2(2 * ms[i])
+        worst = max(worst, e)
+        worst_ratio = max(worst_ratio, e / tol)
+
+    # capture one step in a CUDA graph
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        plan(tf, tg, out=th, work=work)
+        stream.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            plan(tf, tg, out=th, work=work)
+    stream.synchronize()
+
+    def step():
+        graph.replay()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with Clocks(local) as clk:
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for k in range(args.steps):
+                step()
+                ev[k + 1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    t_ms = ev[0].elapsed_time(ev[-1])
+    if pg:
+        t = torch.tensor([t_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_ms = float(t.item())
+        if pg:
+            pg.barrier()
+    convs_total = N_INST * world * args.steps
+    value = convs_total / (t_ms / 1e3)
+    ms_step = t_ms / args.steps
+
+    # end to end through the public API with pinned host buffers
+    hf = torch.tensor(f, dtype=torch.complex64).pin_memory()
+    hg = torch.tensor(g, dtype=torch.complex64).pin_memory()
+    hout = torch.empty_like(hf).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    with torch.cuda.stream(stream):
+        for k in range(2 + e2e_steps):
+            if k == 2:
+                stream.synchronize()
+                t0 = time.perf_counter()
+            tf.copy_(hf, non_blocking=True)
+            tg.copy_(hg, non_blocking=True)
+            plan(tf, tg, out=th, work=work)
+            hout.copy_(th, non_blocking=True)
+        stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+    e2e_val = N_INST * world * e2e_steps / e2e_s if world == 1 else N_INST * e2e_steps / e2e_s * world
+
+    # plain FP64 path: one launch per instance
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        plan64 = dcl.BatchedPlan(ms, dtype=torch.complex128, flags=dcl.api.PLAN_ONE_PER_LAUNCH)
+        tf64, tg64 = tf.to(torch.complex128), tg.to(torch.complex128)
+        th64 = torch.empty_like(tf64)
+        w64 = plan64.workspace(dev)
+        with torch.cuda.stream(stream):
+            plan64(tf64, tg64, out=th64, work=w64)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan64(tf64, tg64, out=th64, work=w64)
+            e1.record(stream)
+        stream.synchronize()
+        t64 = e0.elapsed_time(e1)
+        h64 = th64.cpu().numpy()
+        worst64 = 0.0
+        for i in pick:
+            a, b = off[i], off[i + 1]
+            ref = oracle.padded_complex(f[a:b], g[a:b])
+            worst64 = max(worst64, float(np.linalg.norm(h64[a:b] - ref) / np.linalg.norm(ref)))
+        fp64 = {"convs_per_s": N_INST / (t64 / 1e3), "ms_per_batch": t64, "launches": plan64.launches,
+                "max_rel_l2_sampled": worst64, "tol": 1e-12}
+        del tf64, tg64, th64, w64, plan64
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        n, dt, sample = oracle_convs(ms, f, g, off, budget_s=15.0)
+        cpu = {"value": n / dt, "unit": "convs/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    alg_bytes = 3 * total * 8
+    avg_ms = statistics.mean(per)
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": committed_traffic(alg_bytes), "peak_source": peak_kind,
+            "kernel": "conv1d_kernel<K_COMPLEX,float2> (persistent)",
+            "alg_bytes_per_launch": alg_bytes}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "convs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instances_per_gpu": N_INST, "total_elements_per_gpu": total,
+                       "seed": SEED, "l2": "inputs larger than L2 (%.2f GB per step)" % (alg_bytes / 1e9),
+                       "parallelism": f"{world} independent batches"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "convs/s", "h2d_bytes_per_step": 2 * total * 8,
+                    "d2h_bytes_per_step": total * 8},
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps * plan.launches,
+            "parity": {"max_rel_l2_sampled": worst, "worst_err_over_tol": worst_ratio,
+                       "tol": "5e-7*log2(2m)", "instances_checked": len(pick)},
+            "fp64_plain": fp64,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

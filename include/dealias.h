@@ -1,0 +1,151 @@
+/*
+ * dealias.h -- C ABI of a GB300 (sm_103a) library for implicitly dealiased
+ * linear convolutions, after J. C. Bowman and M. Roberts, "Efficient
+ * Dealiased Convolutions without Padding", SIAM J. Sci. Comput. (2011).
+ *
+ * Every zero-padded DFT of size 2m, 3m or 4m is computed as q sub-transforms
+ * of size m on residues of the padded index (Eqs. (2.1)-(2.2), Sec. 2.2,
+ * Sec. 4.1); the padded array is never formed in device memory.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Arrays are row-major, last dimension contiguous (Sec. 3.1), complex values
+ *   interleaved (re, im).  dtype DC_C64 = complex64 (float32 pairs) computed in
+ *   FP32; DC_C128 = complex128 computed in FP64.  Root-of-unity tables are
+ *   always generated in FP64 and rounded to the working precision.
+ * - f, g, e, w, h, df, dg and work are DEVICE pointers owned by the caller; the
+ *   library never frees them.  They must be aligned to the element size
+ *   (8 bytes for DC_C64, 16 for DC_C128), else DC_ERR_ALIGN.  An output may be
+ *   the same pointer as an input (in place, as in the paper); any other
+ *   overlap is DC_ERR_ARG.
+ * - work is caller-provided device scratch of at least the size that
+ *   dc_workspace_size (or dc_batched_plan_workspace_size) reports, aligned to
+ *   256 bytes; its first 256 bytes hold a device status word.  Two calls that
+ *   may run concurrently must not share a workspace.
+ * - stream is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *   work and return; argument errors are detected on the host and returned
+ *   synchronously, before anything is enqueued.  Errors found by kernels are
+ *   recorded in the workspace status word, read with dc_read_status.
+ * - Sizes: every transform length must be 2^a, 3*2^a or 5*2^a (including 1-5).
+ *   Other sizes return DC_ERR_SIZE.  The first call for a new size builds that
+ *   size's root tables with cudaMalloc and a generator kernel; to keep
+ *   allocation out of a captured CUDA graph, call dc_prepare first.
+ * - Thread safety: calls may come from several host threads; table creation
+ *   is serialized inside the library.
+ */
+#ifndef DEALIAS_H
+#define DEALIAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dc_status;
+#define DC_OK          0
+#define DC_ERR_ARG     1  /* null pointer, bad dtype/kind, negative size, bad overlap */
+#define DC_ERR_SIZE    2  /* size not 2^a, 3*2^a, 5*2^a; odd Hermitian m; too large */
+#define DC_ERR_ALIGN   3  /* pointer not aligned to its element size / workspace to 256 */
+#define DC_ERR_CUDA    4  /* a CUDA runtime call failed (dc_last_cuda_error gives it) */
+#define DC_ERR_TIMEOUT 5  /* a bounded device-side wait ran out (device status word) */
+#define DC_ERR_NOMEM   6  /* workspace smaller than the size the query reports */
+#define DC_ERR_DEVICE  7  /* a kernel's own consistency check failed (device status) */
+
+#define DC_C64  0
+#define DC_C128 1
+
+#define DC_KIND_COMPLEX           0
+#define DC_KIND_HERMITIAN         1
+#define DC_KIND_TERNARY           2
+#define DC_KIND_COMPLEX_ADJOINT   3
+#define DC_KIND_HERMITIAN_ADJOINT 4
+
+/* Human-readable name of a status code (static string). */
+const char* dc_status_string(dc_status s);
+
+/* cudaError_t value of the most recent DC_ERR_CUDA on this host thread. */
+int32_t dc_last_cuda_error(void);
+
+/* Workspace bytes a call of `kind` on the unpadded sizes dims[0..ndim-1] needs.
+ * dims are the unpadded sizes m per dimension (for Hermitian kinds, the
+ * centered dimensions are given as m, not 2m-1).  DC_ERR_SIZE/ARG as above. */
+dc_status dc_workspace_size(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype,
+                            size_t* bytes);
+
+/* Builds the root tables for a call of `kind` on dims (allocates device
+ * memory once per size and device).  Optional; the first call does it too. */
+dc_status dc_prepare(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype);
+
+/* Copies the workspace status word to the host after synchronizing `stream`.
+ * *status = DC_OK or the first error a kernel recorded since the workspace
+ * was last cleared by an entry point; *detail = kernel-specific detail. */
+dc_status dc_read_status(const void* work, void* stream, int32_t* status, int32_t* detail);
+
+/* ---------------------------------------------------------------------------
+ * 1D complex binary convolution (Sec. 2.1, Eqs. (2.1)-(2.2), Function cconv).
+ * f, g: m complex values, Fourier origin at index 0.  Writes the dealiased
+ * linear convolution h_k = sum_{p=0}^{k} f_p g_{k-p}, k = 0..m-1 (N = 2m).
+ * ------------------------------------------------------------------------- */
+dc_status dc_conv_complex_1d(const void* f, const void* g, void* h, int64_t m, int32_t dtype,
+                             void* work, size_t work_bytes, void* stream);
+
+/* 1D centered Hermitian convolution under the 2/3 rule (Sec. 2.3, Function
+ * conv; N = 3m).  f, g hold the wavenumbers 0..m-1 of Hermitian data
+ * (U_{-k} = conj U_k); f_0 is taken as Re f_0 (Hermitian symmetry enforced,
+ * Sec. 5).  h_k = sum_{p=k-m+1}^{m-1} f_p g_{k-p}, k = 0..m-1.  m must be
+ * even (the case m = 2c the paper documents) or 1. */
+dc_status dc_conv_hermitian_1d(const void* f, const void* g, void* h, int64_t m, int32_t dtype,
+                               void* work, size_t work_bytes, void* stream);
+
+/* 1D centered Hermitian ternary convolution (Sec. 4.2, Function tconv;
+ * N = 4m).  h_k = sum_{p+q+r=k} f_p g_q e_r over p,q,r in [-m+1, m-1],
+ * k = 0..m-1; inputs as for dc_conv_hermitian_1d (any m of the allowed form). */
+dc_status dc_conv_ternary_hermitian_1d(const void* f, const void* g, const void* e, void* h,
+                                       int64_t m, int32_t dtype, void* work, size_t work_bytes,
+                                       void* stream);
+
+/* Gradients (no counterpart in the paper; defined for the real loss
+ * L = Re sum_k conj(w_k) h_k with grad = dL/dRe x + i dL/dIm x):
+ * complex:   df_p = sum_{k>=p} w_k conj(g_{k-p}),  dg_q = sum_{k>=q} w_k conj(f_{k-q}),
+ *            computed by the same N = 2m residue machinery with the product
+ *            W^ conj(G^) (a correlation with the conjugate partner).
+ * Hermitian: df = S * conv_hermitian(W, g), dg = S * conv_hermitian(W, f),
+ *            where W = w except W_0 = 2 Re w_0 and S halves index 0.
+ * w, f, g are inputs; df, dg outputs (m values each). */
+dc_status dc_conv_complex_1d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                     void* dg, int64_t m, int32_t dtype, void* work,
+                                     size_t work_bytes, void* stream);
+dc_status dc_conv_hermitian_1d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                       void* dg, int64_t m, int32_t dtype, void* work,
+                                       size_t work_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched 1D complex convolutions of uneven sizes in one persistent launch.
+ * A plan fixes the sizes m[0..n-1] (host array), the dtype and the per-size
+ * kernel configuration; instance i occupies elements [off_i, off_i + m_i) of
+ * the packed arrays f, g, h with off_i = m_0 + ... + m_{i-1}.
+ * flags: bit 0 = autotune the per-size configuration on the current device
+ * (times candidates; needs the GPU idle), bit 1 = force the shared-memory-
+ * resident path only where it fits, bit 2 = one launch per instance (the
+ * "plain" comparison mode).  Planning allocates device memory; execution does
+ * not.  dc_conv_complex_1d_batched may be captured in a CUDA graph.
+ * ------------------------------------------------------------------------- */
+typedef struct dc_batched_plan dc_batched_plan;
+#define DC_PLAN_AUTOTUNE        1
+#define DC_PLAN_ONE_PER_LAUNCH  4
+dc_status dc_batched_plan_create(const int64_t* m, int32_t n, int32_t dtype, int32_t flags,
+                                 dc_batched_plan** plan);
+dc_status dc_batched_plan_workspace_size(const dc_batched_plan* plan, size_t* bytes);
+/* Number of kernel launches one execution of the plan issues. */
+dc_status dc_batched_plan_launches(const dc_batched_plan* plan, int32_t* launches);
+dc_status dc_conv_complex_1d_batched(const dc_batched_plan* plan, const void* f, const void* g,
+                                     void* h, void* work, size_t work_bytes, void* stream);
+dc_status dc_batched_plan_destroy(dc_batched_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEALIAS_H */

@@ -1,0 +1,18 @@
+"""GB300 (sm_103a) implicitly dealiased convolutions (Bowman & Roberts 2011).
+
+The compute path is libdealias.so (hand-written CUDA, C ABI in
+include/dealias.h); this package is its thin PyTorch binding.
+"""
+
+from .api import (  # noqa: F401
+    BatchedPlan,
+    DealiasError,
+    conv_complex_1d,
+    conv_complex_1d_adjoint,
+    conv_hermitian_1d,
+    conv_hermitian_1d_adjoint,
+    conv_ternary_hermitian_1d,
+    prepare,
+    read_status,
+    workspace_size,
+)

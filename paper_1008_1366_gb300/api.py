@@ -1,0 +1,173 @@
+"""PyTorch-facing binding of the C ABI (argument marshalling only).
+
+Every function takes CUDA tensors (complex64 -> FP32 path, complex128 -> FP64
+path), checks shapes on the host, allocates the output and workspace with
+PyTorch's allocator, and calls the matching ``dc_*`` entry point of
+libdealias.so on the current stream.  All arithmetic runs in the library's
+kernels.
+"""
+
+import ctypes
+
+import torch
+
+from . import _native
+
+C64, C128 = 0, 1
+KIND_COMPLEX, KIND_HERMITIAN, KIND_TERNARY, KIND_COMPLEX_ADJOINT, KIND_HERMITIAN_ADJOINT = range(5)
+PLAN_AUTOTUNE = 1
+PLAN_ONE_PER_LAUNCH = 4
+
+
+class DealiasError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+def check(status, what):
+    if status != 0:
+        L = _native.lib()
+        msg = L.dc_status_string(status).decode()
+        if status == 4:
+            msg += f" (cudaError {L.dc_last_cuda_error()})"
+        raise DealiasError(status, f"{what}: {msg}")
+
+
+def dtype_code(t):
+    if t.dtype == torch.complex64:
+        return C64
+    if t.dtype == torch.complex128:
+        return C128
+    raise TypeError(f"expected complex64 or complex128, got {t.dtype}")
+
+
+def _stream(t):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _inputs(*ts):
+    ref = ts[0]
+    if not ref.is_cuda:
+        raise ValueError("inputs must be CUDA tensors (no CPU path exists)")
+    for t in ts:
+        if t.device != ref.device or t.dtype != ref.dtype or t.shape != ref.shape:
+            raise ValueError("inputs must share device, dtype and shape")
+        if not t.is_contiguous():
+            raise ValueError("inputs must be contiguous")
+    return dtype_code(ref)
+
+
+def workspace_size(kind, dims, dtype):
+    d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    out = ctypes.c_size_t(0)
+    check(_native.lib().dc_workspace_size(kind, len(dims), d, dtype, ctypes.byref(out)), "dc_workspace_size")
+    return int(out.value)
+
+
+def prepare(kind, dims, dtype):
+    d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    check(_native.lib().dc_prepare(kind, len(dims), d, dtype), "dc_prepare")
+
+
+def _work(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def read_status(work):
+    st, det = ctypes.c_int32(0), ctypes.c_int32(0)
+    check(_native.lib().dc_read_status(_vp(work), _stream(work), ctypes.byref(st), ctypes.byref(det)),
+          "dc_read_status")
+    return st.value, det.value
+
+
+def _run_1d(name, kind, ins, nout, out):
+    dt = _inputs(*ins)
+    if ins[0].dim() != 1:
+        raise ValueError(f"{name}: expected 1D tensors")
+    m = ins[0].shape[0]
+    outs = list(out) if out is not None else [torch.empty_like(ins[0]) for _ in range(nout)]
+    ws = workspace_size(kind, [m], dt)
+    work = _work(ws, ins[0].device)
+    fn = getattr(_native.lib(), name)
+    args = [_vp(t) for t in ins] + [_vp(t) for t in outs]
+    check(fn(*args, m, dt, _vp(work), ws, _stream(ins[0])), name)
+    return outs[0] if nout == 1 else tuple(outs)
+
+
+def conv_complex_1d(f, g, out=None):
+    """h_k = sum_{p<=k} f_p g_{k-p}, k < m (dc_conv_complex_1d)."""
+    return _run_1d("dc_conv_complex_1d", KIND_COMPLEX, [f, g], 1, None if out is None else [out])
+
+
+def conv_hermitian_1d(f, g, out=None):
+    """Centered Hermitian 2/3-rule convolution (dc_conv_hermitian_1d)."""
+    return _run_1d("dc_conv_hermitian_1d", KIND_HERMITIAN, [f, g], 1, None if out is None else [out])
+
+
+def conv_ternary_hermitian_1d(f, g, e, out=None):
+    """Centered Hermitian ternary convolution (dc_conv_ternary_hermitian_1d)."""
+    return _run_1d("dc_conv_ternary_hermitian_1d", KIND_TERNARY, [f, g, e], 1,
+                   None if out is None else [out])
+
+
+def conv_complex_1d_adjoint(w, f, g):
+    """(df, dg) of L = Re <w, conv_complex_1d(f, g)> (dc_conv_complex_1d_adjoint)."""
+    return _run_1d("dc_conv_complex_1d_adjoint", KIND_COMPLEX_ADJOINT, [w, f, g], 2, None)
+
+
+def conv_hermitian_1d_adjoint(w, f, g):
+    """(df, dg) of L = Re <w, conv_hermitian_1d(f, g)> (dc_conv_hermitian_1d_adjoint)."""
+    return _run_1d("dc_conv_hermitian_1d_adjoint", KIND_HERMITIAN_ADJOINT, [w, f, g], 2, None)
+
+
+class BatchedPlan:
+    """Plan for packed 1D complex convolutions of uneven sizes
+    (dc_batched_plan_create / dc_conv_complex_1d_batched)."""
+
+    def __init__(self, sizes, dtype=torch.complex64, flags=0):
+        self.sizes = [int(x) for x in sizes]
+        self.dtype = dtype
+        self.code = C64 if dtype == torch.complex64 else C128
+        arr = (ctypes.c_int64 * len(self.sizes))(*self.sizes)
+        h = ctypes.c_void_p(0)
+        check(_native.lib().dc_batched_plan_create(arr, len(self.sizes), self.code, flags, ctypes.byref(h)),
+              "dc_batched_plan_create")
+        self.handle = h
+        ws = ctypes.c_size_t(0)
+        check(_native.lib().dc_batched_plan_workspace_size(h, ctypes.byref(ws)), "workspace")
+        self.workspace_bytes = int(ws.value)
+        n = ctypes.c_int32(0)
+        check(_native.lib().dc_batched_plan_launches(h, ctypes.byref(n)), "launches")
+        self.launches = int(n.value)
+        self.total = sum(self.sizes)
+        self._work = None
+
+    def workspace(self, device):
+        if self._work is None or self._work.device != device:
+            self._work = _work(self.workspace_bytes, device)
+        return self._work
+
+    def __call__(self, f, g, out=None, work=None):
+        _inputs(f, g)
+        if f.dim() != 1 or f.shape[0] != self.total or f.dtype != self.dtype:
+            raise ValueError("packed inputs must be 1D of the plan's total length and dtype")
+        out = torch.empty_like(f) if out is None else out
+        work = self.workspace(f.device) if work is None else work
+        check(_native.lib().dc_conv_complex_1d_batched(self.handle, _vp(f), _vp(g), _vp(out), _vp(work),
+                                                       work.numel(), _stream(f)),
+              "dc_conv_complex_1d_batched")
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _native.lib().dc_batched_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None

@@ -1,0 +1,228 @@
+// C ABI entry points (include/dealias.h): argument checks, planning and
+// dispatch to the kernels.  No entry point allocates device memory except
+// the first use of a size (root tables) and plan creation.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "conv1d.cuh"
+#include "launch.h"
+#include "plan.h"
+#include "tables.h"
+
+using namespace dc;
+
+namespace {
+thread_local int32_t t_last_cuda = 0;
+std::mutex g_dev_mu;
+DeviceInfo g_dev[64];
+bool g_dev_ok[64] = {false};
+}  // namespace
+
+extern "C" void dc_set_last_cuda_error(cudaError_t e) { t_last_cuda = (int32_t)e; }
+
+namespace dc {
+const DeviceInfo& device_info() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lock(g_dev_mu);
+  if (!g_dev_ok[dev]) {
+    DeviceInfo d{};
+    d.device = dev;
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&d.l2_bytes, cudaDevAttrL2CacheSize, dev);
+    if (d.sms <= 0) d.sms = 1;
+    if (d.smem_optin <= 0) d.smem_optin = 48 * 1024;
+    g_dev[dev] = d;
+    g_dev_ok[dev] = true;
+  }
+  return g_dev[dev];
+}
+}  // namespace dc
+
+namespace {
+
+constexpr size_t kHeader = sizeof(WorkHeader);
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int dsize_of(int32_t dtype) { return dtype == DC_C64 ? 8 : dtype == DC_C128 ? 16 : 0; }
+
+int smem_budget() { return device_info().smem_optin - kStaticSmemReserve; }
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Output may equal an input exactly; partial overlap is an error.
+bool bad_overlap(const void* o, const void* i, size_t bytes) {
+  if (!o || !i || o == i) return false;
+  const char* a = (const char*)o;
+  const char* b = (const char*)i;
+  return a < b + bytes && b < a + bytes;
+}
+
+dc_status check_ptrs(const void* const* ins, int nin, void* const* outs, int nout, size_t bytes,
+                     int ds) {
+  for (int x = 0; x < nin; ++x) {
+    if (!ins[x]) return DC_ERR_ARG;
+    if (!aligned(ins[x], ds)) return DC_ERR_ALIGN;
+  }
+  for (int o = 0; o < nout; ++o) {
+    if (!outs[o]) return DC_ERR_ARG;
+    if (!aligned(outs[o], ds)) return DC_ERR_ALIGN;
+    for (int x = 0; x < nin; ++x)
+      if (bad_overlap(outs[o], ins[x], bytes)) return DC_ERR_ARG;
+    for (int p = 0; p < o; ++p)
+      if (outs[p] == outs[o] || bad_overlap(outs[o], outs[p], bytes)) return DC_ERR_ARG;
+  }
+  return DC_OK;
+}
+
+dc_status check_work(void* work, size_t have, size_t need) {
+  if (!work) return DC_ERR_ARG;
+  if (!aligned(work, 256)) return DC_ERR_ALIGN;
+  if (have < need) return DC_ERR_NOMEM;
+  return DC_OK;
+}
+
+// Plans one 1D call; fills cfg (with its table) and the workspace size.
+dc_status plan_1d(int kind, int64_t m, int ds, bool with_table, CfgDev* cfg, size_t* work) {
+  if (m < 1) return DC_ERR_ARG;
+  if (!make_cfg(kind, m, ds, kThreads, smem_budget(), 0, cfg)) return DC_ERR_SIZE;
+  if (with_table) {
+    const void* tw = nullptr;
+    dc_status st = get_root_table(cfg->TN, ds, &tw);
+    if (st != DC_OK) return st;
+    cfg->tw = tw;
+  }
+  *work = kHeader + align_up(cfg_scratch_bytes(kind, *cfg, ds), 256);
+  return DC_OK;
+}
+
+dc_status run_1d(int kind, const void* const* ins, int nin, void* const* outs, int nout, int64_t m,
+                 int32_t dtype, void* work, size_t work_bytes, void* stream) {
+  const int ds = dsize_of(dtype);
+  if (!ds || m < 1) return DC_ERR_ARG;
+  dc_status st = check_ptrs(ins, nin, outs, nout, (size_t)m * ds, ds);
+  if (st != DC_OK) return st;
+  CfgDev cfg;
+  size_t need = 0;
+  st = plan_1d(kind, m, ds, true, &cfg, &need);
+  if (st != DC_OK) return st;
+  if ((st = check_work(work, work_bytes, need)) != DC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  ConvArgs a{};
+  for (int x = 0; x < nin; ++x) a.in[x] = ins[x];
+  for (int o = 0; o < nout; ++o) a.out[o] = outs[o];
+  a.nitems = 1;
+  a.ninst = 1;
+  a.hdr = (WorkHeader*)work;
+  a.scratch = (char*)work + kHeader;
+  a.slot_bytes = (int64_t)align_up(cfg_scratch_bytes(kind, cfg, ds), 256);
+  a.cfg0 = cfg;
+  DC_CUDA_TRY(cudaMemsetAsync(work, 0, kHeader, s));
+  return launch_conv1d(kind, ds, a, 1, cfg.smem, s);
+}
+
+int kind_of_public(int32_t k) {
+  switch (k) {
+    case DC_KIND_COMPLEX: return K_COMPLEX;
+    case DC_KIND_HERMITIAN: return K_HERMITIAN;
+    case DC_KIND_TERNARY: return K_TERNARY;
+    case DC_KIND_COMPLEX_ADJOINT: return K_COMPLEX_ADJ;
+    case DC_KIND_HERMITIAN_ADJOINT: return K_HERMITIAN_ADJ;
+  }
+  return -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dc_status_string(dc_status s) {
+  switch (s) {
+    case DC_OK: return "ok";
+    case DC_ERR_ARG: return "invalid argument";
+    case DC_ERR_SIZE: return "unsupported size";
+    case DC_ERR_ALIGN: return "misaligned pointer";
+    case DC_ERR_CUDA: return "CUDA runtime error";
+    case DC_ERR_TIMEOUT: return "device-side wait timed out";
+    case DC_ERR_NOMEM: return "workspace too small";
+    case DC_ERR_DEVICE: return "device-side check failed";
+  }
+  return "unknown status";
+}
+
+int32_t dc_last_cuda_error(void) { return t_last_cuda; }
+
+dc_status dc_workspace_size(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype,
+                            size_t* bytes) {
+  const int ds = dsize_of(dtype);
+  const int k = kind_of_public(kind);
+  if (!ds || k < 0 || !dims || !bytes || ndim < 1) return DC_ERR_ARG;
+  if (ndim != 1) return DC_ERR_ARG;
+  CfgDev cfg;
+  return plan_1d(k, dims[0], ds, false, &cfg, bytes);
+}
+
+dc_status dc_prepare(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype) {
+  const int ds = dsize_of(dtype);
+  const int k = kind_of_public(kind);
+  if (!ds || k < 0 || !dims || ndim != 1) return DC_ERR_ARG;
+  CfgDev cfg;
+  size_t need;
+  return plan_1d(k, dims[0], ds, true, &cfg, &need);
+}
+
+dc_status dc_read_status(const void* work, void* stream, int32_t* status, int32_t* detail) {
+  if (!work || !status) return DC_ERR_ARG;
+  WorkHeader h;
+  DC_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  DC_CUDA_TRY(cudaMemcpy(&h, work, sizeof(h), cudaMemcpyDeviceToHost));
+  *status = h.status;
+  if (detail) *detail = h.detail;
+  return DC_OK;
+}
+
+dc_status dc_conv_complex_1d(const void* f, const void* g, void* h, int64_t m, int32_t dtype,
+                             void* work, size_t work_bytes, void* stream) {
+  const void* ins[2] = {f, g};
+  void* outs[1] = {h};
+  return run_1d(K_COMPLEX, ins, 2, outs, 1, m, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_hermitian_1d(const void* f, const void* g, void* h, int64_t m, int32_t dtype,
+                               void* work, size_t work_bytes, void* stream) {
+  const void* ins[2] = {f, g};
+  void* outs[1] = {h};
+  return run_1d(K_HERMITIAN, ins, 2, outs, 1, m, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_ternary_hermitian_1d(const void* f, const void* g, const void* e, void* h,
+                                       int64_t m, int32_t dtype, void* work, size_t work_bytes,
+                                       void* stream) {
+  const void* ins[3] = {f, g, e};
+  void* outs[1] = {h};
+  return run_1d(K_TERNARY, ins, 3, outs, 1, m, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_complex_1d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                     void* dg, int64_t m, int32_t dtype, void* work,
+                                     size_t work_bytes, void* stream) {
+  const void* ins[3] = {w, f, g};
+  void* outs[2] = {df, dg};
+  return run_1d(K_COMPLEX_ADJ, ins, 3, outs, 2, m, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_hermitian_1d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                       void* dg, int64_t m, int32_t dtype, void* work,
+                                       size_t work_bytes, void* stream) {
+  const void* ins[3] = {w, f, g};
+  void* outs[2] = {df, dg};
+  return run_1d(K_HERMITIAN_ADJ, ins, 3, outs, 2, m, dtype, work, work_bytes, stream);
+}
+
+}  // extern "C"
