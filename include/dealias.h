@@ -94,8 +94,10 @@ dc_status dc_conv_complex_1d(const void* f, const void* g, void* h, int64_t m, i
 /* 1D centered Hermitian convolution under the 2/3 rule (Sec. 2.3, Function
  * conv; N = 3m).  f, g hold the wavenumbers 0..m-1 of Hermitian data
  * (U_{-k} = conj U_k); f_0 is taken as Re f_0 (Hermitian symmetry enforced,
- * Sec. 5).  h_k = sum_{p=k-m+1}^{m-1} f_p g_{k-p}, k = 0..m-1.  m must be
- * even (the case m = 2c the paper documents) or 1. */
+ * Sec. 5).  h_k = sum_{p=k-m+1}^{m-1} f_p g_{k-p}, k = 0..m-1.  Any m of
+ * the allowed form, odd or even: the sub-transforms are full complex
+ * transforms of w^f + i w^g, so the odd case m = 2c+1 (which the paper leaves
+ * undocumented) needs no special treatment. */
 dc_status dc_conv_hermitian_1d(const void* f, const void* g, void* h, int64_t m, int32_t dtype,
                                void* work, size_t work_bytes, void* stream);
 
@@ -120,6 +122,44 @@ dc_status dc_conv_complex_1d_adjoint(const void* w, const void* f, const void* g
 dc_status dc_conv_hermitian_1d_adjoint(const void* w, const void* f, const void* g, void* df,
                                        void* dg, int64_t m, int32_t dtype, void* work,
                                        size_t work_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * 2D and 3D convolutions (Sec. 3).  Layout row-major, last axis contiguous.
+ * Complex (Functions cconv2, cconv3; N = 2m per axis): f, g, h of shape
+ *   (mx, my) or (mx, my, mz); h_k = sum_{0<=p<=k} f_p g_{k-p} componentwise.
+ * Centered Hermitian (Function conv2 and the 3D analogue; N = 3m per axis):
+ *   shape (2mx-1, my) or (2mx-1, 2my-1, mz); the leading axes are centered
+ *   (index i <-> wavenumber i - (m-1)), the last axis holds wavenumbers
+ *   0..m-1 and U_{-k} = conj U_k for the whole wave vector.  The last-axis-0
+ *   row (2D) / plane (3D) is projected onto that symmetry before convolving
+ *   (U(k',0) <- (U(k',0) + conj U(-k',0))/2, Sec. 5); inputs are not modified.
+ *   h_k = sum_p f_p g_{k-p} over p with |p_d|, |k_d - p_d| <= m_d - 1.
+ * Gradients as for 1D (same loss convention); for Hermitian data the
+ *   upstream array is symmetrized on the last-axis-0 row/plane,
+ *   W(k',0) = w(k',0) + conj w(-k',0), and the outputs are halved there.
+ * dims: mx, my (, mz) are the unpadded sizes (for Hermitian, m not 2m-1).
+ * ------------------------------------------------------------------------- */
+dc_status dc_conv_complex_2d(const void* f, const void* g, void* h, int64_t mx, int64_t my,
+                             int32_t dtype, void* work, size_t work_bytes, void* stream);
+dc_status dc_conv_complex_3d(const void* f, const void* g, void* h, int64_t mx, int64_t my,
+                             int64_t mz, int32_t dtype, void* work, size_t work_bytes, void* stream);
+dc_status dc_conv_hermitian_2d(const void* f, const void* g, void* h, int64_t mx, int64_t my,
+                               int32_t dtype, void* work, size_t work_bytes, void* stream);
+dc_status dc_conv_hermitian_3d(const void* f, const void* g, void* h, int64_t mx, int64_t my,
+                               int64_t mz, int32_t dtype, void* work, size_t work_bytes,
+                               void* stream);
+dc_status dc_conv_complex_2d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                     void* dg, int64_t mx, int64_t my, int32_t dtype, void* work,
+                                     size_t work_bytes, void* stream);
+dc_status dc_conv_complex_3d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                     void* dg, int64_t mx, int64_t my, int64_t mz, int32_t dtype,
+                                     void* work, size_t work_bytes, void* stream);
+dc_status dc_conv_hermitian_2d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                       void* dg, int64_t mx, int64_t my, int32_t dtype, void* work,
+                                       size_t work_bytes, void* stream);
+dc_status dc_conv_hermitian_3d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                       void* dg, int64_t mx, int64_t my, int64_t mz, int32_t dtype,
+                                       void* work, size_t work_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched 1D complex convolutions of uneven sizes in one persistent launch.

@@ -9,6 +9,10 @@ from .api import (  # noqa: F401
     DealiasError,
     conv_complex_1d,
     conv_complex_1d_adjoint,
+    conv_complex_nd,
+    conv_complex_nd_adjoint,
+    conv_hermitian_nd,
+    conv_hermitian_nd_adjoint,
     conv_hermitian_1d,
     conv_hermitian_1d_adjoint,
     conv_ternary_hermitian_1d,

@@ -27,6 +27,14 @@ SIGNATURES = {
     "dc_conv_ternary_hermitian_1d": [_vp, _vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_complex_1d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_hermitian_1d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_complex_2d": [_vp, _vp, _vp, _i64, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_complex_3d": [_vp, _vp, _vp, _i64, _i64, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_hermitian_2d": [_vp, _vp, _vp, _i64, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_hermitian_3d": [_vp, _vp, _vp, _i64, _i64, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_complex_2d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_complex_3d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i64, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_hermitian_2d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_hermitian_3d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i64, _i64, _i32, _vp, _sz, _vp],
     "dc_batched_plan_create": [ctypes.POINTER(_i64), _i32, _i32, _i32, ctypes.POINTER(_vp)],
     "dc_batched_plan_workspace_size": [_vp, ctypes.POINTER(_sz)],
     "dc_batched_plan_launches": [_vp, ctypes.POINTER(_i32)],

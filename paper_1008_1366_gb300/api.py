@@ -125,6 +125,51 @@ def conv_hermitian_1d_adjoint(w, f, g):
     return _run_1d("dc_conv_hermitian_1d_adjoint", KIND_HERMITIAN_ADJOINT, [w, f, g], 2, None)
 
 
+def _dims(t, hermitian):
+    """Unpadded sizes of a multi-D array (centered Hermitian axes hold 2m-1)."""
+    shape = list(t.shape)
+    if not hermitian:
+        return shape
+    for n in shape[:-1]:
+        if n % 2 != 1:
+            raise ValueError("centered Hermitian axes hold 2m-1 entries")
+    return [(n + 1) // 2 for n in shape[:-1]] + [shape[-1]]
+
+
+def _run_md(name, kind, ins, nout, hermitian):
+    dt = _inputs(*ins)
+    if ins[0].dim() not in (2, 3):
+        raise ValueError(f"{name}: expected 2D or 3D tensors")
+    dims = _dims(ins[0], hermitian)
+    outs = [torch.empty_like(ins[0]) for _ in range(nout)]
+    ws = workspace_size(kind, dims, dt)
+    work = _work(ws, ins[0].device)
+    fn = getattr(_native.lib(), name)
+    args = [_vp(t) for t in ins] + [_vp(t) for t in outs] + list(dims)
+    check(fn(*args, dt, _vp(work), ws, _stream(ins[0])), name)
+    return outs[0] if nout == 1 else tuple(outs)
+
+
+def conv_complex_nd(f, g):
+    """2D/3D complex convolution (dc_conv_complex_2d / _3d)."""
+    return _run_md(f"dc_conv_complex_{f.dim()}d", KIND_COMPLEX, [f, g], 1, False)
+
+
+def conv_hermitian_nd(f, g):
+    """2D/3D centered Hermitian convolution (dc_conv_hermitian_2d / _3d)."""
+    return _run_md(f"dc_conv_hermitian_{f.dim()}d", KIND_HERMITIAN, [f, g], 1, True)
+
+
+def conv_complex_nd_adjoint(w, f, g):
+    """(df, dg) for the 2D/3D complex convolution."""
+    return _run_md(f"dc_conv_complex_{f.dim()}d_adjoint", KIND_COMPLEX_ADJOINT, [w, f, g], 2, False)
+
+
+def conv_hermitian_nd_adjoint(w, f, g):
+    """(df, dg) for the 2D/3D centered Hermitian convolution."""
+    return _run_md(f"dc_conv_hermitian_{f.dim()}d_adjoint", KIND_HERMITIAN_ADJOINT, [w, f, g], 2, True)
+
+
 class BatchedPlan:
     """Plan for packed 1D complex convolutions of uneven sizes
     (dc_batched_plan_create / dc_conv_complex_1d_batched)."""

@@ -9,6 +9,7 @@
 
 #include "conv1d.cuh"
 #include "launch.h"
+#include "multid.h"
 #include "plan.h"
 #include "tables.h"
 
@@ -127,6 +128,22 @@ dc_status run_1d(int kind, const void* const* ins, int nin, void* const* outs, i
   return launch_conv1d(kind, ds, a, 1, cfg.smem, s);
 }
 
+dc_status run_md(int32_t pk, int ndim, const int64_t* dims, const void* const* ins, int nin,
+                 void* const* outs, int nout, int32_t dtype, void* work, size_t work_bytes,
+                 void* stream) {
+  const int ds = dsize_of(dtype);
+  if (!ds) return DC_ERR_ARG;
+  for (int d = 0; d < ndim; ++d) if (dims[d] < 1) return DC_ERR_ARG;
+  const bool herm = pk == DC_KIND_HERMITIAN || pk == DC_KIND_HERMITIAN_ADJOINT;
+  int64_t n = 1;
+  for (int d = 0; d < ndim; ++d) n *= (herm && d < ndim - 1) ? 2 * dims[d] - 1 : dims[d];
+  dc_status st = check_ptrs(ins, nin, outs, nout, (size_t)n * ds, ds);
+  if (st != DC_OK) return st;
+  if (!work) return DC_ERR_ARG;
+  if (!aligned(work, 256)) return DC_ERR_ALIGN;
+  return md_run(pk, ndim, dims, ds, ins, nin, outs, nout, work, work_bytes, (cudaStream_t)stream);
+}
+
 int kind_of_public(int32_t k) {
   switch (k) {
     case DC_KIND_COMPLEX: return K_COMPLEX;
@@ -162,8 +179,8 @@ dc_status dc_workspace_size(int32_t kind, int32_t ndim, const int64_t* dims, int
                             size_t* bytes) {
   const int ds = dsize_of(dtype);
   const int k = kind_of_public(kind);
-  if (!ds || k < 0 || !dims || !bytes || ndim < 1) return DC_ERR_ARG;
-  if (ndim != 1) return DC_ERR_ARG;
+  if (!ds || k < 0 || !dims || !bytes || ndim < 1 || ndim > 3) return DC_ERR_ARG;
+  if (ndim > 1) return md_workspace(kind, ndim, dims, ds, bytes);
   CfgDev cfg;
   return plan_1d(k, dims[0], ds, false, &cfg, bytes);
 }
@@ -171,7 +188,8 @@ dc_status dc_workspace_size(int32_t kind, int32_t ndim, const int64_t* dims, int
 dc_status dc_prepare(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype) {
   const int ds = dsize_of(dtype);
   const int k = kind_of_public(kind);
-  if (!ds || k < 0 || !dims || ndim != 1) return DC_ERR_ARG;
+  if (!ds || k < 0 || !dims || ndim < 1 || ndim > 3) return DC_ERR_ARG;
+  if (ndim > 1) return md_prepare(kind, ndim, dims, ds);
   CfgDev cfg;
   size_t need;
   return plan_1d(k, dims[0], ds, true, &cfg, &need);
@@ -223,6 +241,75 @@ dc_status dc_conv_hermitian_1d_adjoint(const void* w, const void* f, const void*
   const void* ins[3] = {w, f, g};
   void* outs[2] = {df, dg};
   return run_1d(K_HERMITIAN_ADJ, ins, 3, outs, 2, m, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_complex_2d(const void* f, const void* g, void* h, int64_t mx, int64_t my,
+                             int32_t dtype, void* work, size_t work_bytes, void* stream) {
+  const void* ins[2] = {f, g};
+  void* outs[1] = {h};
+  const int64_t d[2] = {mx, my};
+  return run_md(DC_KIND_COMPLEX, 2, d, ins, 2, outs, 1, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_complex_3d(const void* f, const void* g, void* h, int64_t mx, int64_t my,
+                             int64_t mz, int32_t dtype, void* work, size_t work_bytes, void* stream) {
+  const void* ins[2] = {f, g};
+  void* outs[1] = {h};
+  const int64_t d[3] = {mx, my, mz};
+  return run_md(DC_KIND_COMPLEX, 3, d, ins, 2, outs, 1, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_hermitian_2d(const void* f, const void* g, void* h, int64_t mx, int64_t my,
+                               int32_t dtype, void* work, size_t work_bytes, void* stream) {
+  const void* ins[2] = {f, g};
+  void* outs[1] = {h};
+  const int64_t d[2] = {mx, my};
+  return run_md(DC_KIND_HERMITIAN, 2, d, ins, 2, outs, 1, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_hermitian_3d(const void* f, const void* g, void* h, int64_t mx, int64_t my,
+                               int64_t mz, int32_t dtype, void* work, size_t work_bytes,
+                               void* stream) {
+  const void* ins[2] = {f, g};
+  void* outs[1] = {h};
+  const int64_t d[3] = {mx, my, mz};
+  return run_md(DC_KIND_HERMITIAN, 3, d, ins, 2, outs, 1, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_complex_2d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                     void* dg, int64_t mx, int64_t my, int32_t dtype, void* work,
+                                     size_t work_bytes, void* stream) {
+  const void* ins[3] = {w, f, g};
+  void* outs[2] = {df, dg};
+  const int64_t d[2] = {mx, my};
+  return run_md(DC_KIND_COMPLEX_ADJOINT, 2, d, ins, 3, outs, 2, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_complex_3d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                     void* dg, int64_t mx, int64_t my, int64_t mz, int32_t dtype,
+                                     void* work, size_t work_bytes, void* stream) {
+  const void* ins[3] = {w, f, g};
+  void* outs[2] = {df, dg};
+  const int64_t d[3] = {mx, my, mz};
+  return run_md(DC_KIND_COMPLEX_ADJOINT, 3, d, ins, 3, outs, 2, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_hermitian_2d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                       void* dg, int64_t mx, int64_t my, int32_t dtype, void* work,
+                                       size_t work_bytes, void* stream) {
+  const void* ins[3] = {w, f, g};
+  void* outs[2] = {df, dg};
+  const int64_t d[2] = {mx, my};
+  return run_md(DC_KIND_HERMITIAN_ADJOINT, 2, d, ins, 3, outs, 2, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_hermitian_3d_adjoint(const void* w, const void* f, const void* g, void* df,
+                                       void* dg, int64_t mx, int64_t my, int64_t mz, int32_t dtype,
+                                       void* work, size_t work_bytes, void* stream) {
+  const void* ins[3] = {w, f, g};
+  void* outs[2] = {df, dg};
+  const int64_t d[3] = {mx, my, mz};
+  return run_md(DC_KIND_HERMITIAN_ADJOINT, 3, d, ins, 3, outs, 2, dtype, work, work_bytes, stream);
 }
 
 }  // extern "C"

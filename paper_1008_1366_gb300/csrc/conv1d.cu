@@ -38,6 +38,7 @@ dc_status launch_conv1d(int kind, int dsize, const ConvArgs& a, int grid, int sm
       case K_TERNARY:       return launch_t<K_TERNARY, float2>(a, grid, smem, s);
       case K_COMPLEX_ADJ:   return launch_t<K_COMPLEX_ADJ, float2>(a, grid, smem, s);
       case K_HERMITIAN_ADJ: return launch_t<K_HERMITIAN_ADJ, float2>(a, grid, smem, s);
+      case K_HERMITIAN_PAIR: return launch_t<K_HERMITIAN_PAIR, float2>(a, grid, smem, s);
     }
   } else {
     switch (kind) {
@@ -46,6 +47,7 @@ dc_status launch_conv1d(int kind, int dsize, const ConvArgs& a, int grid, int sm
       case K_TERNARY:       return launch_t<K_TERNARY, double2>(a, grid, smem, s);
       case K_COMPLEX_ADJ:   return launch_t<K_COMPLEX_ADJ, double2>(a, grid, smem, s);
       case K_HERMITIAN_ADJ: return launch_t<K_HERMITIAN_ADJ, double2>(a, grid, smem, s);
+      case K_HERMITIAN_PAIR: return launch_t<K_HERMITIAN_PAIR, double2>(a, grid, smem, s);
     }
   }
   return DC_ERR_ARG;
@@ -61,6 +63,7 @@ dc_status conv1d_blocks_per_sm(int kind, int dsize, int smem, int* out) {
     case K_TERNARY: DC_PICK(K_TERNARY); break;
     case K_COMPLEX_ADJ: DC_PICK(K_COMPLEX_ADJ); break;
     case K_HERMITIAN_ADJ: DC_PICK(K_HERMITIAN_ADJ); break;
+    case K_HERMITIAN_PAIR: DC_PICK(K_HERMITIAN_PAIR); break;
     default: return DC_ERR_ARG;
   }
 #undef DC_PICK

@@ -201,6 +201,28 @@ template <class C> struct KP<K_HERMITIAN_ADJ, C> {
   }
 };
 
+// rows of the multi-D Hermitian gradient: two plain Hermitian convolutions
+// (W, g) -> out 0 and (W, f) -> out 1 sharing the transforms of W; the
+// symmetrization of W and the halving act on the whole multi-D array and are
+// done by the outer passes.
+template <class C> struct KP<K_HERMITIAN_PAIR, C> {
+  static constexpr int Q = 3, NARR = 2, NFWD = 2;
+  __device__ static C build(const C* const* in, int x, int k, int ri, int m, const C* tw) {
+    const int r = ri - 1;
+    if (x == 0) {
+      C ww = herm_w(in[0], k, r, m, tw, real_part(in[0][0]));
+      C wf = herm_w(in[1], k, r, m, tw, real_part(in[1][0]));
+      return pack_i(ww, wf);
+    }
+    return herm_w(in[2], k, r, m, tw, real_part(in[2][0]));
+  }
+  __device__ static void pointwise(C* v) { KP<K_HERMITIAN_ADJ, C>::pointwise(v); }
+  __device__ static C contrib(int o, C X, int k, int ri, int m, const C* tw) {
+    return KP<K_HERMITIAN_ADJ, C>::contrib(o, X, k, ri, m, tw);
+  }
+  __device__ static C finish(int o, C a, int k, int m) { return KP<K_HERMITIAN, C>::finish(o, a, k, m); }
+};
+
 // ---------------------------------------------------------------------------
 // level 1: `count` instances of one size, each wholly in shared memory
 // ---------------------------------------------------------------------------

@@ -1,0 +1,241 @@
+// 2D and 3D implicitly dealiased convolutions (Sec. 3) composed from the
+// outer-axis passes (axis.cu) and the batched row kernels (conv1d.cuh).
+//
+//   2D (Functions cconv2, conv2): x-backward of each input into q_x residue
+//     arrays (m_x rows each) -> one 1D convolution along y per row of every
+//     residue array (in place) -> x-forward recombining the residues.
+//   3D (Function cconv3 and the centered Hermitian analogue): x-backward ->
+//     for every x-row slab a 2D convolution in (y, z), itself y-backward ->
+//     rows along z -> y-forward written back into the slab -> x-forward.
+// The (y, z) work arrays are decoupled from the data, as the paper stresses
+// (Sec. 1, Sec. 3.1): slabs are processed in chunks whose work arrays fit in
+// a fixed budget (sized for L2 residency) and are reused chunk after chunk.
+// Gradients use the same composition with three transformed inputs
+// (w, f, g) and the gradient row kernels; for Hermitian data the upstream
+// array is symmetrized on the self-conjugate subspace on load and the outputs
+// halved there on store.
+#include <algorithm>
+
+#include "conv1d.cuh"
+#include "launch.h"
+#include "multid.h"
+#include "plan.h"
+#include "tables.h"
+
+namespace dc {
+namespace {
+
+constexpr size_t kHeader = sizeof(WorkHeader);
+constexpr size_t kChunkBudget = 64ull << 20;   // bytes of (y, z) work arrays per chunk
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Md {
+  int pk = 0, ndim = 0, ds = 0;
+  int64_t m[3] = {0, 0, 0};
+  bool herm = false, adj = false;
+  int qa = 2, narr = 2, nout = 1, row_kind = K_COMPLEX;
+  int64_t ny_in = 0;          // stored y extent (3D): my or 2my-1
+  int64_t nx = 0;             // elements of one x-level residue array
+  int64_t slabs = 0, sx = 0;  // 3D: slabs and elements per slab
+  int64_t S = 0;              // 3D: slabs per chunk
+  AxisArgs ax, ay;            // outer-axis templates (plan, tile width, table)
+  CfgDev rows;                // row configuration
+  int rows_grid = 1;
+  size_t rows_slot = 0;
+  size_t off_y = 0, off_rows = 0, total = 0;
+};
+
+int smem_cap() { return device_info().smem_optin - kStaticSmemReserve; }
+
+bool axis_cfg(bool centered, int64_t m, int ds, bool with_table, AxisArgs* a) {
+  const int emax = ds == 8 ? 24 : 12;
+  FftPlan p;
+  if (m < 1 || m > (1 << 16) || !make_fft_plan((int)m, emax, &p)) return false;
+  if (p.tpt > 512) return false;
+  const int colb = axis_smem(true, centered, (int)m, 1, ds);
+  int w = 1;
+  while (w * 2 <= 32 && (w * 2) * p.tpt <= 512 && (w * 2) * colb <= smem_cap()) w *= 2;
+  if (colb > smem_cap()) return false;
+  *a = AxisArgs{};
+  a->m = (int32_t)m;
+  a->centered = centered ? 1 : 0;
+  a->w = w;
+  a->p = p;
+  a->TN = (int32_t)((centered ? 3 : 2) * m);
+  if (with_table) {
+    const void* tw = nullptr;
+    if (get_root_table(a->TN, ds, &tw) != DC_OK) return false;
+    a->tw = tw;
+  }
+  return true;
+}
+
+dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_tables, Md* md) {
+  if (ndim < 2 || ndim > 3) return DC_ERR_ARG;
+  for (int d = 0; d < ndim; ++d) {
+    if (dims[d] < 1) return DC_ERR_ARG;
+    md->m[d] = dims[d];
+  }
+  md->pk = pk; md->ndim = ndim; md->ds = ds;
+  md->herm = pk == DC_KIND_HERMITIAN || pk == DC_KIND_HERMITIAN_ADJOINT;
+  md->adj = pk == DC_KIND_COMPLEX_ADJOINT || pk == DC_KIND_HERMITIAN_ADJOINT;
+  if (pk == DC_KIND_TERNARY || pk < 0 || pk > 4) return DC_ERR_ARG;
+  md->qa = md->herm ? 3 : 2;
+  md->narr = md->adj ? 3 : 2;
+  md->nout = md->adj ? 2 : 1;
+  md->row_kind = md->herm ? (md->adj ? K_HERMITIAN_PAIR : K_HERMITIAN)
+                          : (md->adj ? K_COMPLEX_ADJ : K_COMPLEX);
+  const int64_t mx = md->m[0], my = md->m[1], mlast = md->m[ndim - 1];
+  if (!axis_cfg(md->herm, mx, ds, with_tables, &md->ax)) return DC_ERR_SIZE;
+  int64_t nrows;   // rows of the row kernel per launch
+  if (ndim == 2) {
+    md->nx = mx * my;
+    nrows = md->qa * mx;
+  } else {
+    if (!axis_cfg(md->herm, my, ds, with_tables, &md->ay)) return DC_ERR_SIZE;
+    md->ny_in = md->herm ? 2 * my - 1 : my;
+    md->nx = mx * md->ny_in * mlast;
+    md->slabs = md->qa * mx;
+    md->sx = md->ny_in * mlast;
+    const size_t per_slab = (size_t)md->narr * md->qa * my * mlast * ds;
+    md->S = std::max<int64_t>(1, std::min<int64_t>(md->slabs, kChunkBudget / per_slab));
+    nrows = md->qa * md->S * my;
+  }
+  if (!make_cfg(md->row_kind, mlast, ds, kThreads, smem_cap(), 0, &md->rows)) return DC_ERR_SIZE;
+  if (with_tables) {
+    const void* tw = nullptr;
+    dc_status st = get_root_table(md->rows.TN, ds, &tw);
+    if (st != DC_OK) return st;
+    md->rows.tw = tw;
+  }
+  int bps = 1;
+  if (with_tables) {
+    dc_status st = conv1d_blocks_per_sm(md->row_kind, ds, md->rows.smem, &bps);
+    if (st != DC_OK) return st;
+  }
+  const int64_t nitems = (nrows + md->rows.nt - 1) / md->rows.nt;
+  md->rows_grid = (int)std::max<int64_t>(1, std::min<int64_t>(nitems, (int64_t)std::max(1, bps) * device_info().sms));
+  if (!with_tables) md->rows_grid = (int)std::min<int64_t>(nitems, 4 * 1024);   // upper bound for sizing
+  md->rows_slot = align_up(cfg_scratch_bytes(md->row_kind, md->rows, ds), 256);
+  size_t off = kHeader + align_up((size_t)md->narr * md->qa * md->nx * ds, 256);
+  md->off_y = off;
+  if (ndim == 3) off += align_up((size_t)md->narr * md->qa * md->S * my * mlast * ds, 256);
+  md->off_rows = off;
+  off += (size_t)md->rows_grid * md->rows_slot;
+  md->total = off;
+  return DC_OK;
+}
+
+dc_status run_rows(const Md& md, const void* const* in, void* const* out, int64_t nrows, char* work,
+                   cudaStream_t s) {
+  ConvArgs a{};
+  for (int x = 0; x < 3; ++x) a.in[x] = in[x];
+  for (int o = 0; o < 2; ++o) a.out[o] = out[o];
+  a.stride = md.m[md.ndim - 1];
+  a.ninst = (int32_t)nrows;
+  a.nitems = (int32_t)((nrows + md.rows.nt - 1) / md.rows.nt);
+  a.hdr = (WorkHeader*)work;
+  a.scratch = work + md.off_rows;
+  a.slot_bytes = (int64_t)md.rows_slot;
+  a.cfg0 = md.rows;
+  const int grid = std::min(md.rows_grid, a.nitems);
+  return launch_conv1d(md.row_kind, md.ds, a, grid, md.rows.smem, s);
+}
+
+}  // namespace
+
+dc_status md_workspace(int pk, int ndim, const int64_t* dims, int ds, size_t* bytes) {
+  Md md;
+  dc_status st = plan_md(pk, ndim, dims, ds, false, &md);
+  if (st == DC_OK) *bytes = md.total;
+  return st;
+}
+
+dc_status md_prepare(int pk, int ndim, const int64_t* dims, int ds) {
+  Md md;
+  return plan_md(pk, ndim, dims, ds, true, &md);
+}
+
+dc_status md_run(int pk, int ndim, const int64_t* dims, int ds, const void* const* ins, int nin,
+                 void* const* outs, int nout, void* work, size_t work_bytes, cudaStream_t s) {
+  Md md;
+  dc_status st = plan_md(pk, ndim, dims, ds, true, &md);
+  if (st != DC_OK) return st;
+  if (nin != md.narr || nout != md.nout) return DC_ERR_ARG;
+  if (work_bytes < md.total) return DC_ERR_NOMEM;
+  char* wk = (char*)work;
+  char* X = wk + kHeader;
+  const int64_t mx = md.m[0], my = md.m[1], mz = md.m[md.ndim - 1];
+  const int qa = md.qa;
+  auto xres = [&](int z, int r) { return (void*)(X + ((size_t)z * qa + r) * md.nx * ds); };
+  // slot of gradient output o inside the transformed arrays (w, f, g): f -> df, g -> dg
+  const int oslot0 = md.adj ? 1 : 0;
+  DC_CUDA_TRY(cudaMemsetAsync(work, 0, kHeader, s));
+
+  // x-backward
+  AxisArgs ax = md.ax;
+  ax.outer = 1;
+  ax.inner = md.ndim == 2 ? my : md.ny_in * mz;
+  ax.proj = md.herm ? md.ndim : 0;
+  ax.proj_mz = mz;
+  ax.proj_ny = md.ndim == 3 ? md.ny_in : 1;
+  ax.dbl_mask = (pk == DC_KIND_HERMITIAN_ADJOINT) ? 1 : 0;
+  for (int z = 0; z < md.narr; ++z) {
+    ax.in[z] = ins[z];
+    for (int r = 0; r < qa; ++r) ax.out[z * 3 + r] = xres(z, r);
+  }
+  if ((st = launch_axis(false, ds, ax, md.narr, s)) != DC_OK) return st;
+
+  if (md.ndim == 2) {
+    const void* rin[3] = {nullptr, nullptr, nullptr};
+    void* rout[2] = {nullptr, nullptr};
+    for (int z = 0; z < md.narr; ++z) rin[z] = xres(z, 0);
+    for (int o = 0; o < md.nout; ++o) rout[o] = xres(oslot0 + o, 0);
+    if ((st = run_rows(md, rin, rout, (int64_t)qa * mx, wk, s)) != DC_OK) return st;
+  } else {
+    char* Y = wk + md.off_y;
+    for (int64_t s0 = 0; s0 < md.slabs; s0 += md.S) {
+      const int64_t Sc = std::min<int64_t>(md.S, md.slabs - s0);
+      const size_t ych = (size_t)Sc * my * mz;   // elements of one y-level residue array
+      auto yres = [&](int z, int r) { return (void*)(Y + ((size_t)z * qa + r) * ych * ds); };
+      AxisArgs ay = md.ay;
+      ay.outer = Sc;
+      ay.inner = mz;
+      for (int z = 0; z < md.narr; ++z) {
+        ay.in[z] = X + ((size_t)z * qa * md.nx + (size_t)s0 * md.sx) * ds;
+        for (int r = 0; r < qa; ++r) ay.out[z * 3 + r] = yres(z, r);
+      }
+      if ((st = launch_axis(false, ds, ay, md.narr, s)) != DC_OK) return st;
+      const void* rin[3] = {nullptr, nullptr, nullptr};
+      void* rout[2] = {nullptr, nullptr};
+      for (int z = 0; z < md.narr; ++z) rin[z] = yres(z, 0);
+      for (int o = 0; o < md.nout; ++o) rout[o] = yres(oslot0 + o, 0);
+      if ((st = run_rows(md, rin, rout, (int64_t)qa * Sc * my, wk, s)) != DC_OK) return st;
+      AxisArgs yf = md.ay;
+      yf.outer = Sc;
+      yf.inner = mz;
+      for (int o = 0; o < md.nout; ++o) {
+        for (int r = 0; r < qa; ++r) yf.fin[o * 3 + r] = yres(oslot0 + o, r);
+        yf.fout[o] = X + ((size_t)(oslot0 + o) * qa * md.nx + (size_t)s0 * md.sx) * ds;
+      }
+      if ((st = launch_axis(true, ds, yf, md.nout, s)) != DC_OK) return st;
+    }
+  }
+
+  // x-forward
+  AxisArgs xf = md.ax;
+  xf.outer = 1;
+  xf.inner = ax.inner;
+  xf.proj = ax.proj;
+  xf.proj_mz = ax.proj_mz;
+  xf.proj_ny = ax.proj_ny;
+  xf.halve_mask = (pk == DC_KIND_HERMITIAN_ADJOINT) ? 3 : 0;
+  for (int o = 0; o < md.nout; ++o) {
+    for (int r = 0; r < qa; ++r) xf.fin[o * 3 + r] = xres(oslot0 + o, r);
+    xf.fout[o] = outs[o];
+  }
+  return launch_axis(true, ds, xf, md.nout, s);
+}
+
+}  // namespace dc

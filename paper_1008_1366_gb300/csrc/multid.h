@@ -1,0 +1,44 @@
+// Multi-dimensional composition: outer-axis implicit passes (axis.cu) and
+// the batched row kernels (conv1d.cuh).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+#include "../../include/dealias.h"
+
+namespace dc {
+
+struct AxisArgs {
+  const void* in[3];      // backward: arrays to transform (blockIdx.y selects)
+  void* out[9];           // backward: out[array * 3 + residue], layout (outer, m, inner)
+  const void* fin[9];     // forward: fin[output * 3 + residue], layout (outer, m, inner)
+  void* fout[3];          // forward: outputs, layout (outer, m or 2m-1, inner)
+  int64_t outer, inner;
+  int64_t proj_mz, proj_ny;   // 3D self-conjugate plane geometry (inner = proj_ny * proj_mz)
+  int32_t m;              // unpadded size along the axis
+  int32_t centered;       // 0: complex q = 2; 1: centered q = 3
+  int32_t proj;           // 0: none; 2: 2D column ky = 0; 3: 3D plane kz = 0
+  int32_t w;              // columns per block
+  int32_t dbl_mask;       // backward arrays whose self-conjugate subspace is U(k) + conj U(-k)
+  int32_t halve_mask;     // forward outputs scaled by 1/2 on the self-conjugate subspace
+  int32_t TN, pad;
+  const void* tw;         // zeta_TN^i, TN = 2m or 3m
+  FftPlan p;              // length-m sub-transform plan
+};
+
+inline int axis_smem(bool forward, int centered, int m, int w, int ds) {
+  const int nout = centered ? 2 * m - 1 : m;
+  return (forward ? (m + nout) : m) * w * ds;
+}
+
+dc_status launch_axis(bool forward, int dsize, const AxisArgs& a, int narrays, cudaStream_t s);
+
+// public multi-D kinds handled by multid.cu
+dc_status md_workspace(int pkind, int ndim, const int64_t* dims, int ds, size_t* bytes);
+dc_status md_prepare(int pkind, int ndim, const int64_t* dims, int ds);
+dc_status md_run(int pkind, int ndim, const int64_t* dims, int ds, const void* const* ins, int nin,
+                 void* const* outs, int nout, void* work, size_t work_bytes, cudaStream_t s);
+
+}  // namespace dc

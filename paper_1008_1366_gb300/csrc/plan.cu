@@ -13,6 +13,7 @@ KindShape kind_shape(int kind) {
     case K_TERNARY:       return {2, 2, 1, 3, 1};
     case K_COMPLEX_ADJ:   return {2, 3, 2, 3, 2};
     case K_HERMITIAN_ADJ: return {3, 2, 2, 3, 2};
+    case K_HERMITIAN_PAIR: return {3, 2, 2, 3, 2};
   }
   return {0, 0, 0, 0, 0};
 }
@@ -23,7 +24,8 @@ int64_t kind_L(int kind, int64_t m) { return kind == K_TERNARY ? 2 * m : m; }
 int64_t kind_TN(int kind, int64_t m) {
   switch (kind) {
     case K_HERMITIAN:
-    case K_HERMITIAN_ADJ: return 3 * m;
+    case K_HERMITIAN_ADJ:
+    case K_HERMITIAN_PAIR: return 3 * m;
     case K_TERNARY:       return 4 * m;
     default:              return 2 * m;
   }

@@ -18,6 +18,8 @@ enum Kind : int32_t {
   K_TERNARY = 2,       // centered Hermitian ternary convolution, N = 4m (Sec. 4.2)
   K_COMPLEX_ADJ = 3,   // gradient of K_COMPLEX: correlations with conj partners
   K_HERMITIAN_ADJ = 4, // gradient of K_HERMITIAN
+  K_HERMITIAN_PAIR = 5,// two Hermitian convolutions (W, g) and (W, f) sharing W (rows of
+                       // the multi-D Hermitian gradient)
 };
 
 // Shape of one kind: q residues, NARR shared-memory arrays per residue
