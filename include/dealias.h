@@ -123,6 +123,24 @@ dc_status dc_conv_hermitian_1d_adjoint(const void* w, const void* f, const void*
                                        void* dg, int64_t m, int32_t dtype, void* work,
                                        size_t work_bytes, void* stream);
 
+/* dc_conv_complex_1d without a workspace (no counterpart in the paper).
+ * Same arguments and result as dc_conv_complex_1d, minus work/work_bytes.
+ * For callers that cannot allocate device memory: code that runs under a CUDA
+ * stream capture in global mode (cudaMalloc is prohibited there), code whose
+ * device memory belongs to an allocator it may not bypass, and real-time loops
+ * that cannot afford cudaMalloc's implicit synchronization.  It calls no
+ * cudaMalloc, cudaFree or allocating routine: its scratch is one fixed 2 MiB
+ * device array inside the library, held by every GPU that loads the library
+ * until the process exits.  Limit: m <= 40960 for DC_C64 and m <= 20480 for
+ * DC_C128; larger m returns DC_ERR_SIZE.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array, and each call rebuilds its root table and clears its status
+ * word there, so calls whose GPU work may overlap (different streams, or
+ * concurrent host threads) race and must be serialized by the caller. */
+dc_status dc_conv_complex_1d_noalloc(const void* f, const void* g, void* h, int64_t m,
+                                     int32_t dtype, void* stream);
+
 /* ---------------------------------------------------------------------------
  * 2D and 3D convolutions (Sec. 3).  Layout row-major, last axis contiguous.
  * Complex (Functions cconv2, cconv3; N = 2m per axis): f, g, h of shape

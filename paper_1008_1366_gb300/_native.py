@@ -27,6 +27,7 @@ SIGNATURES = {
     "dc_conv_ternary_hermitian_1d": [_vp, _vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_complex_1d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_hermitian_1d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_complex_1d_noalloc": [_vp, _vp, _vp, _i64, _i32, _vp],
     "dc_conv_complex_2d": [_vp, _vp, _vp, _i64, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_complex_3d": [_vp, _vp, _vp, _i64, _i64, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_hermitian_2d": [_vp, _vp, _vp, _i64, _i64, _i32, _vp, _sz, _vp],

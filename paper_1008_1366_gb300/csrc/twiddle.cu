@@ -28,6 +28,15 @@ std::mutex g_mu;
 std::map<std::tuple<int, int64_t, int>, void*> g_tables;
 }
 
+dc_status launch_gen_roots(void* out, int64_t TN, int dsize, cudaStream_t s) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((TN + threads - 1) / threads);
+  if (dsize == 8) gen_roots_kernel<float2><<<blocks, threads, 0, s>>>((float2*)out, TN);
+  else gen_roots_kernel<double2><<<blocks, threads, 0, s>>>((double2*)out, TN);
+  DC_CUDA_TRY(cudaGetLastError());
+  return DC_OK;
+}
+
 dc_status get_root_table(int64_t TN, int dsize, const void** out) {
   int dev = 0;
   DC_CUDA_TRY(cudaGetDevice(&dev));
