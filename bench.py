@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--suite", action="store_true",
+                   help="measure every configuration of the scope, one JSON line each")
     p.add_argument("--instances", type=int, default=N_INST,
                    help="batch size (default 4096; smaller batches are for profiling only)")
     return p.parse_args()
@@ -190,11 +192,124 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _time_call(fn, reps, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), ts
+
+
+def one_sided_sigma(ts):
+    """Mean T and the one-sided deviations sigma_L, sigma_H (Sec. 2.1 timing
+    statistic, read with the square root over the whole quotient)."""
+    T = statistics.mean(ts)
+    n = len(ts)
+    d = max(n / 2 - 1, 1)
+    lo = sum((t - T) ** 2 for t in ts if t < T)
+    hi = sum((t - T) ** 2 for t in ts if t > T)
+    return T, (lo / d) ** 0.5, (hi / d) ** 0.5
+
+
+def run_suite(args):
+    """Every configuration of the scope: time (CUDA events, median of reps),
+    convolutions/s, algorithmic GB/s and fraction of the measured HBM peak,
+    and parity against the FP64 oracle.  One JSON object per line."""
+    import torch
+    import oracle
+    import paper_1008_1366_gb300 as dcl
+    from paper_1008_1366_gb300 import autograd, synthetic
+    peak, _ = measured_peak_hbm()
+    dev = torch.device("cuda", 0)
+
+    def emit(name, ms, ts, nbytes, err, tol, extra=None):
+        T, sl, sh = one_sided_sigma(ts)
+        rec = {"config": name, "ms_median": ms, "ms_mean": T, "sigma_L": sl, "sigma_H": sh,
+               "convs_per_s": 1e3 / ms, "alg_bytes": nbytes, "gbs": nbytes / ms / 1e6,
+               "hbm_frac_of_measured": nbytes / ms / 1e6 / peak, "rel_l2": err, "tol": tol}
+        if extra:
+            rec.update(extra)
+        print(json.dumps(rec), flush=True)
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a).ravel() - np.asarray(b).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+
+    reps = max(5, args.steps)
+    # 1: 1D complex, m = 1024, complex128
+    f = synthetic.uniform_complex(1024, 1009)
+    g = synthetic.uniform_complex(1024, 1010)
+    tf, tg = (torch.tensor(x, dtype=torch.complex128, device=dev) for x in (f, g))
+    ms, ts = _time_call(lambda: dcl.conv_complex_1d(tf, tg), reps)
+    emit("1D complex m=1024 c128", ms, ts, 3 * 1024 * 16,
+         rel(dcl.conv_complex_1d(tf, tg).cpu().numpy(), oracle.direct_complex(f, g)), 1e-12)
+    # 2a: 1D Hermitian m = 2^16; 2b: ternary m = 2^14
+    m = 1 << 16
+    f = synthetic.hermitian_spectrum((m,), 1.0, 1010)
+    g = synthetic.hermitian_spectrum((m,), 1.0, 1011)
+    ref = oracle.padded_hermitian(f, g)
+    for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 5e-7 * np.log2(3 * m))):
+        tf, tg = (torch.tensor(x, dtype=dt, device=dev) for x in (f, g))
+        ms, ts = _time_call(lambda: dcl.conv_hermitian_1d(tf, tg), reps)
+        emit(f"1D Hermitian m=2^16 {dt}", ms, ts, 3 * m * tf.element_size(),
+             rel(dcl.conv_hermitian_1d(tf, tg).cpu().numpy(), ref), tol)
+    m = 1 << 14
+    fs = [synthetic.hermitian_spectrum((m,), 1.0, 1010 + s) for s in range(3)]
+    ref = oracle.padded_ternary_hermitian(*fs)
+    for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 5e-7 * np.log2(4 * m))):
+        ts_ = [torch.tensor(x, dtype=dt, device=dev) for x in fs]
+        ms, ts = _time_call(lambda: dcl.conv_ternary_hermitian_1d(*ts_), reps)
+        emit(f"1D ternary Hermitian m=2^14 {dt}", ms, ts, 4 * m * ts_[0].element_size(),
+             rel(dcl.conv_ternary_hermitian_1d(*ts_).cpu().numpy(), ref), tol)
+    # 3a: 2D Hermitian 1024 x 1024 (2047 x 1024), 3b: 2D complex 2048^2, complex64
+    shape = synthetic.hermitian_shape((1024, 1024))
+    f = synthetic.hermitian_spectrum(shape, 1.5, 1011)
+    g = synthetic.hermitian_spectrum(shape, 1.5, 1012)
+    tf, tg = (torch.tensor(x, dtype=torch.complex64, device=dev) for x in (f, g))
+    ms, ts = _time_call(lambda: dcl.conv_hermitian_nd(tf, tg), reps)
+    emit("2D Hermitian 2047x1024 c64", ms, ts, 3 * f.size * 8,
+         rel(dcl.conv_hermitian_nd(tf, tg).cpu().numpy(), oracle.padded_hermitian(f, g)),
+         5e-7 * np.log2(9 * 1024 * 1024))
+    f = synthetic.uniform_complex((2048, 2048), 1013)
+    g = synthetic.uniform_complex((2048, 2048), 1014)
+    tf, tg = (torch.tensor(x, dtype=torch.complex64, device=dev) for x in (f, g))
+    ms, ts = _time_call(lambda: dcl.conv_complex_nd(tf, tg), reps)
+    emit("2D complex 2048x2048 c64", ms, ts, 3 * f.size * 8,
+         rel(dcl.conv_complex_nd(tf, tg).cpu().numpy(), oracle.padded_complex(f, g)),
+         5e-7 * np.log2(4 * 2048 * 2048))
+    # 5: 3D Hermitian 511 x 511 x 256, forward and backward (both gradients)
+    shape = synthetic.hermitian_shape((256, 256, 256))
+    f = synthetic.hermitian_spectrum(shape, 11 / 6, 1015)
+    g = synthetic.hermitian_spectrum(shape, 11 / 6, 1016)
+    w = synthetic.uniform_complex(shape, 1017)
+    tf, tg, tw = (torch.tensor(x, dtype=torch.complex64, device=dev) for x in (f, g, w))
+    ms, ts = _time_call(lambda: dcl.conv_hermitian_nd(tf, tg), max(3, reps // 2))
+    h = dcl.conv_hermitian_nd(tf, tg).cpu().numpy()
+    r = np.random.default_rng(0)
+    pts = [tuple(int(r.integers(0, n)) for n in shape) for _ in range(6)]
+    err = np.abs(np.array([h[p] for p in pts]) - oracle.hermitian_at(f, g, pts))
+    est = float(np.sqrt(h.size * np.mean(err ** 2)) / np.linalg.norm(h))
+    emit("3D Hermitian 511x511x256 c64 forward", ms, ts, 3 * f.size * 8, est,
+         5e-7 * np.log2(27 * 256 ** 3), {"rel_l2_estimate": "from 6 uniformly random sampled outputs"})
+    ms, ts = _time_call(lambda: dcl.conv_hermitian_nd_adjoint(tw, tf, tg), max(3, reps // 2))
+    emit("3D Hermitian 511x511x256 c64 backward (df, dg)", ms, ts, 5 * f.size * 8, None, None)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.suite:
+        run_suite(args)
         return
 
     import torch

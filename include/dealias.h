@@ -198,6 +198,14 @@ dc_status dc_batched_plan_create(const int64_t* m, int32_t n, int32_t dtype, int
 dc_status dc_batched_plan_workspace_size(const dc_batched_plan* plan, size_t* bytes);
 /* Number of kernel launches one execution of the plan issues. */
 dc_status dc_batched_plan_launches(const dc_batched_plan* plan, int32_t* launches);
+/* Configuration chosen for the i-th distinct size of the plan (sizes in
+ * increasing order): *level 1 = whole sub-transform in shared memory with *nt
+ * instances per block, 2 = two-level m = l1 * l2 through scratch with column
+ * tiles of width *w.  Any output pointer may be NULL.  DC_ERR_ARG if i is out
+ * of range. */
+dc_status dc_batched_plan_describe(const dc_batched_plan* plan, int32_t i, int64_t* m,
+                                   int32_t* level, int32_t* nt, int32_t* l1, int32_t* l2,
+                                   int32_t* w);
 dc_status dc_conv_complex_1d_batched(const dc_batched_plan* plan, const void* f, const void* g,
                                      void* h, void* work, size_t work_bytes, void* stream);
 dc_status dc_batched_plan_destroy(dc_batched_plan* plan);

@@ -192,6 +192,20 @@ class BatchedPlan:
         self.total = sum(self.sizes)
         self._work = None
 
+    def describe(self):
+        """Per distinct size: (m, level, instances per block, L1, L2, tile width)."""
+        out = []
+        i = 0
+        while True:
+            m, vals = ctypes.c_int64(0), [ctypes.c_int32(0) for _ in range(5)]
+            st = _native.lib().dc_batched_plan_describe(self.handle, i, ctypes.byref(m),
+                                                        *[ctypes.byref(v) for v in vals])
+            if st != 0:
+                break
+            out.append((m.value,) + tuple(v.value for v in vals))
+            i += 1
+        return out
+
     def workspace(self, device):
         if self._work is None or self._work.device != device:
             self._work = _work(self.workspace_bytes, device)

@@ -17,6 +17,17 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdealias.so")
 
 SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu"]
+# the fused 1D kernel, one translation unit per (kind, precision)
+INSTANCES = [(k, tag, c) for k in range(6) for tag, c in (("f", "float2"), ("d", "double2"))]
+
+
+def _units():
+    units = [(n, n.replace(".cu", ".o"), []) for n in SOURCES]
+    for k, tag, c in INSTANCES:
+        units.append(("conv1d_inst.cu", f"conv1d_k{k}_{tag}.o",
+                      [f"-DDC_INST_KIND={k}", f"-DDC_INST_C={c}", f"-DDC_INST_TAG={tag}"]))
+    return units
+
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--use_fast_math=false"]
@@ -54,20 +65,24 @@ def build(verbose=False, jobs=None, extra_flags=()):
     headers = _headers()
     flags = [f for f in FLAGS if not f.startswith("--use_fast_math")] + list(extra_flags)
 
-    def compile_one(name):
+    def compile_one(unit):
+        name, objname, defs = unit
         src = os.path.join(CSRC, name)
-        obj = os.path.join(BUILD, name.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, objname)
         if not _stale(obj, src, headers):
             return obj, ""
-        cmd = [nvcc] + ARCH + flags + ["-I", INCLUDE, "-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + flags + defs + ["-I", INCLUDE, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {name}:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed for {objname}:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
         return obj, r.stdout + r.stderr
 
-    jobs = jobs or min(len(SOURCES), os.cpu_count() or 4)
+    units = _units()
+    jobs = jobs or min(len(units), os.cpu_count() or 4)
+    # longest units first
+    units.sort(key=lambda u: 0 if u[0] == "conv1d_inst.cu" else 1)
     with ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+        results = list(ex.map(compile_one, units))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:

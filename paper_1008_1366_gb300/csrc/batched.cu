@@ -2,11 +2,13 @@
 //
 // Planning groups the instances by size; each size gets a configuration
 // (level 1: `nt` instances per block wholly in shared memory; level 2: one
-// instance per block through a scratch slot).  Work items (a group of same-
-// size instances, or one large instance) are sorted by estimated cost,
-// largest first, and a persistent grid of (SMs x resident blocks) takes them
-// from an atomic counter, which balances uneven sizes like a longest-
-// processing-time schedule.
+// instance per block through a scratch slot).  With DC_PLAN_AUTOTUNE the
+// configuration of every size is chosen by timing the candidates of
+// enumerate_cfgs on the device, on that size's own instance count.  Work
+// items (a group of same-size instances, or one large instance) are sorted
+// by estimated cost, largest first, and a persistent grid of
+// (SMs x resident blocks) takes them from an atomic counter, which balances
+// uneven sizes like a longest-processing-time schedule.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -43,6 +45,88 @@ double item_cost(const CfgDev& c, int count) {
   if (c.level == 2) f *= 1.5;
   return f;
 }
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+// Times one configuration on `count` instances of size m: persistent launch
+// over the instances' items, median of three runs (ms); < 0 on failure.
+float time_cfg(const CfgDev& c, int count, int ds, const void* f, const void* g, void* h, cudaStream_t s) {
+  std::vector<Item> items;
+  const int per = c.level == 1 ? c.nt : 1;
+  for (int i = 0; i < count; i += per) items.push_back(Item{0, i, std::min(per, count - i), 0});
+  int bps = 1;
+  if (conv1d_blocks_per_sm(K_COMPLEX, ds, c.smem, &bps) != DC_OK || bps < 1) return -1;
+  const int grid = bps * device_info().sms;
+  const size_t slot = align_up(cfg_scratch_bytes(K_COMPLEX, c, ds), 256);
+  DevBuf dcfg, ditems, dwork;
+  if (cudaMalloc(&dcfg.p, sizeof(CfgDev)) != cudaSuccess) return -1;
+  if (cudaMalloc(&ditems.p, items.size() * sizeof(Item)) != cudaSuccess) return -1;
+  if (cudaMalloc(&dwork.p, sizeof(WorkHeader) + (size_t)grid * slot) != cudaSuccess) return -1;
+  cudaMemcpy(dcfg.p, &c, sizeof(CfgDev), cudaMemcpyHostToDevice);
+  cudaMemcpy(ditems.p, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice);
+  ConvArgs a{};
+  a.in[0] = f;
+  a.in[1] = g;
+  a.out[0] = h;
+  a.stride = c.m;
+  a.items = (const Item*)ditems.p;
+  a.nitems = (int32_t)items.size();
+  a.ninst = count;
+  a.cfgs = (const CfgDev*)dcfg.p;
+  a.hdr = (WorkHeader*)dwork.p;
+  a.scratch = (char*)dwork.p + sizeof(WorkHeader);
+  a.slot_bytes = (int64_t)slot;
+  a.persistent = 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<float> t;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaMemsetAsync(dwork.p, 0, sizeof(WorkHeader), s);
+    cudaEventRecord(e0, s);
+    if (launch_conv1d(K_COMPLEX, ds, a, grid, c.smem, s) != DC_OK) break;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) t.push_back(ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess || t.size() < 3) return -1;
+  std::sort(t.begin(), t.end());
+  return t[1];
+}
+
+dc_status autotune_size(int64_t m, int count, int ds, int smem_max, CfgDev* best) {
+  CfgDev cands[24];
+  const int nc = enumerate_cfgs(K_COMPLEX, m, ds, kThreads, smem_max, cands, 24);
+  if (nc <= 1) return DC_OK;
+  const int cnt = std::max(1, std::min(count, 4096));
+  const size_t bytes = (size_t)cnt * m * ds;
+  DevBuf f, g, h;
+  DC_CUDA_TRY(cudaMalloc(&f.p, bytes));
+  DC_CUDA_TRY(cudaMalloc(&g.p, bytes));
+  DC_CUDA_TRY(cudaMalloc(&h.p, bytes));
+  DC_CUDA_TRY(cudaMemset(f.p, 0x3c, bytes));   // finite, normal values
+  DC_CUDA_TRY(cudaMemset(g.p, 0x3b, bytes));
+  cudaStream_t s;
+  DC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  float tbest = -1;
+  for (int k = 0; k < nc; ++k) {
+    const void* tw = nullptr;
+    if (get_root_table(cands[k].TN, ds, &tw) != DC_OK) continue;
+    cands[k].tw = tw;
+    const float t = time_cfg(cands[k], cnt, ds, f.p, g.p, h.p, s);
+    if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; *best = cands[k]; }
+  }
+  cudaStreamDestroy(s);
+  cudaGetLastError();
+  return DC_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -72,6 +156,10 @@ dc_status dc_batched_plan_create(const int64_t* m, int32_t n, int32_t dtype, int
   for (auto& kv : by_size) {
     CfgDev c;
     if (!make_cfg(K_COMPLEX, kv.first, ds, kThreads, smem_max, 0, &c)) { delete p; return DC_ERR_SIZE; }
+    if ((flags & DC_PLAN_AUTOTUNE) && !one) {
+      dc_status st = autotune_size(kv.first, (int)kv.second.size(), ds, smem_max, &c);
+      if (st != DC_OK) { delete p; return st; }
+    }
     const void* tw = nullptr;
     dc_status st = get_root_table(c.TN, ds, &tw);
     if (st != DC_OK) { delete p; return st; }
@@ -138,6 +226,19 @@ dc_status dc_batched_plan_workspace_size(const dc_batched_plan* p, size_t* bytes
 dc_status dc_batched_plan_launches(const dc_batched_plan* p, int32_t* launches) {
   if (!p || !launches) return DC_ERR_ARG;
   *launches = (p->flags & DC_PLAN_ONE_PER_LAUNCH) ? (int32_t)p->items.size() : 1;
+  return DC_OK;
+}
+
+dc_status dc_batched_plan_describe(const dc_batched_plan* p, int32_t i, int64_t* m, int32_t* level,
+                                   int32_t* nt, int32_t* l1, int32_t* l2, int32_t* w) {
+  if (!p || i < 0 || i >= (int32_t)p->cfgs.size()) return DC_ERR_ARG;
+  const CfgDev& c = p->cfgs[i];
+  if (m) *m = c.m;
+  if (level) *level = c.level;
+  if (nt) *nt = c.nt;
+  if (l1) *l1 = c.L1;
+  if (l2) *l2 = c.L2;
+  if (w) *w = c.w;
   return DC_OK;
 }
 

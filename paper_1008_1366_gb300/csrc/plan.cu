@@ -89,6 +89,64 @@ static int largest_divisor_at_most(int n, int cap) {
   return 1;
 }
 
+// Plan of the fused engine (fft2.cuh): one E per size family (8 for 2^a,
+// 12 for 3*2^a, 10 for 5*2^a; larger E spills registers), the odd
+// radix first.  Returns a plan with E = 0 (DFT by definition, one thread per
+// element) when L is not a multiple of E.
+bool make_fused_plan(int L, int dsize, FftPlan* out) {
+  int a, b, c;
+  if (!factor(L, &a, &b, &c)) return false;
+  FftPlan p{};
+  p.L = L;
+  int E, pmax;
+  if (dsize == 8) {
+    if (c) { E = 20; pmax = 4; } else if (b) { E = 12; pmax = 4; } else { E = 16; pmax = 16; }
+  } else {
+    if (c) { E = 10; pmax = 2; } else if (b) { E = 12; pmax = 4; } else { E = 8; pmax = 8; }
+  }
+  if (L % E != 0 || L < E) {
+    p.E = 0;
+    p.tpt = L;
+    p.ns = 0;
+    *out = p;
+    return true;
+  }
+  int ns = 0;
+  if (c) p.r[ns++] = 5;
+  if (b) p.r[ns++] = 3;
+  int lg = 0;
+  while ((1 << (lg + 1)) <= pmax) ++lg;
+  int rem = a;
+  while (rem >= lg) { p.r[ns++] = (int8_t)(1 << lg); rem -= lg; }
+  if (rem > 0) p.r[ns++] = (int8_t)(1 << rem);
+  if (ns > kMaxStages) return false;
+  if (ns == 1) {          // one stage: the DFT by definition is as cheap
+    p.E = 0;
+    p.tpt = L;
+    p.ns = 0;
+    *out = p;
+    return true;
+  }
+  p.ns = ns;
+  p.E = E;
+  p.tpt = L / E;
+  *out = p;
+  return true;
+}
+
+static int64_t padded(int64_t n, int dsize) { return n + (n >> (dsize == 8 ? 4 : 3)) + 1; }
+
+// bytes of the two shared-memory root tables for TN (rounded to an even
+// number of entries), as the kernel lays them out
+static int64_t roots_bytes(int64_t TN, int dsize) {
+  int lg = 0;
+  while ((1ll << lg) < TN) ++lg;
+  const int sh = (lg + 1) / 2;
+  const int64_t S = 1ll << sh;
+  const int64_t ent = S + ((TN + S - 1) >> sh) + 2;
+  return ((ent + 1) & ~1ll) * dsize;
+}
+
 bool make_cfg(int kind, int64_t m, int dsize, int threads, int smem_max, int force_level,
               CfgDev* out) {
   const KindShape ks = kind_shape(kind);
@@ -97,44 +155,48 @@ bool make_cfg(int kind, int64_t m, int dsize, int threads, int smem_max, int for
   if (L > (1 << 20)) return false;
   int a, b, c;
   if (!factor(L, &a, &b, &c)) return false;
-  const int emax = dsize == 8 ? 24 : 12;   // FP64: radix <= 8, E <= 12 (register budget)
   CfgDev cfg{};
   cfg.m = (int32_t)m;
   cfg.L = (int32_t)L;
   cfg.TN = (int32_t)TN;
-  const int64_t mout = m;
+  const int64_t rb = roots_bytes(TN, dsize);
+  const int64_t avail = smem_max - rb;
 
   if (force_level != 2) {
     FftPlan p;
-    if (make_fft_plan((int)L, emax, &p) && p.tpt <= threads) {
-      const int64_t per = (int64_t)(ks.narr * L + ks.nfwd * mout) * dsize;
-      int64_t nt = std::min<int64_t>(threads / p.tpt, smem_max / per);
+    if (make_fused_plan((int)L, dsize, &p) && p.tpt <= threads) {
+      const int64_t per = p.E ? (ks.narr * padded(L, dsize) + ks.nfwd * padded(m, dsize)) * dsize
+                              : (ks.narr * L + ks.nfwd * m) * dsize;
+      const int64_t nt = std::min<int64_t>(threads / p.tpt, avail / per);
       if (nt >= 1) {
         cfg.level = 1;
         cfg.p = p;
         cfg.nt = (int32_t)nt;
-        cfg.smem = (int32_t)(nt * per);
+        cfg.smem = (int32_t)(rb + nt * per);
         *out = cfg;
         return true;
       }
     }
     if (force_level == 1) return false;
   }
-  // two-level: L = L1 * L2 with L2 <= L1, both of the allowed form
+  // two-level: L = L1 * L2 with L2 <= L1, both with fused (non-direct) plans
   int bestL2 = 0;
-  for (int64_t L2 = 1; L2 * L2 <= L; ++L2) {
+  FftPlan pr{}, pc{};
+  for (int64_t L2 = 2; L2 * L2 <= L; ++L2) {
     if (L % L2) continue;
-    int x, y, z;
-    if (factor(L2, &x, &y, &z) && factor(L / L2, &x, &y, &z)) bestL2 = (int)L2;
+    FftPlan tr, tc;
+    if (!make_fused_plan((int)(L / L2), dsize, &tr) || !make_fused_plan((int)L2, dsize, &tc)) continue;
+    if (!tr.E || !tc.E || tr.tpt > threads || tc.tpt > threads) continue;
+    bestL2 = (int)L2;
+    pr = tr;
+    pc = tc;
   }
   if (bestL2 < 1) return false;
   const int L2 = bestL2, L1 = (int)(L / L2);
-  FftPlan pr, pc;
-  if (!make_fft_plan(L1, emax, &pr) || !make_fft_plan(L2, emax, &pc)) return false;
-  if (pr.tpt > threads || pc.tpt > threads) return false;
   const int64_t colbytes = (int64_t)L2 * dsize;
-  int wcap = (int)std::min<int64_t>(threads / pc.tpt, smem_max / ((1 + ks.nfwd) * colbytes));
-  int ncap = (int)std::min<int64_t>(threads / pr.tpt, smem_max / ((int64_t)ks.narr * L1 * dsize));
+  const int64_t rowbytes = padded(L1, dsize) * dsize;
+  const int wcap = (int)std::min<int64_t>(threads / pc.tpt, avail / ((1 + ks.nfwd) * colbytes));
+  const int ncap = (int)std::min<int64_t>(threads / pr.tpt, avail / (ks.narr * rowbytes));
   if (wcap < 1 || ncap < 1) return false;
   const int w = largest_divisor_at_most(L1, std::min(wcap, 64));
   const int nr = largest_divisor_at_most(L2, ncap);
@@ -146,10 +208,56 @@ bool make_cfg(int kind, int64_t m, int dsize, int threads, int smem_max, int for
   cfg.pr = pr;
   cfg.pc = pc;
   cfg.nt = 1;
-  cfg.smem = (int32_t)std::max<int64_t>((1 + ks.nfwd) * w * colbytes,
-                                        (int64_t)ks.narr * nr * L1 * dsize);
+  cfg.smem = (int32_t)(rb + std::max<int64_t>((1 + ks.nfwd) * w * colbytes, ks.narr * nr * rowbytes));
   *out = cfg;
   return true;
+}
+
+int enumerate_cfgs(int kind, int64_t m, int dsize, int threads, int smem_max, CfgDev* out, int maxn) {
+  const KindShape ks = kind_shape(kind);
+  int n = 0;
+  CfgDev base;
+  if (!make_cfg(kind, m, dsize, threads, smem_max, 0, &base)) return 0;
+  out[n++] = base;
+  const int64_t L = kind_L(kind, m), TN = kind_TN(kind, m);
+  const int64_t rb = roots_bytes(TN, dsize), avail = smem_max - rb;
+  // level 1 with fewer instances per block (more blocks per SM)
+  if (base.level == 1) {
+    for (int nt = base.nt / 2; nt >= 1 && n < maxn; nt /= 2) {
+      CfgDev c = base;
+      const int64_t per = (base.smem - rb) / base.nt;
+      c.nt = nt;
+      c.smem = (int32_t)(rb + nt * per);
+      out[n++] = c;
+    }
+  }
+  // level 2 with other splits and tile widths (also for sizes that fit level 1)
+  for (int64_t L2 = 2; L2 * L2 <= L && n < maxn; ++L2) {
+    if (L % L2) continue;
+    FftPlan pr, pc;
+    if (!make_fused_plan((int)(L / L2), dsize, &pr) || !make_fused_plan((int)L2, dsize, &pc)) continue;
+    if (!pr.E || !pc.E || pr.tpt > threads || pc.tpt > threads) continue;
+    const int L1 = (int)(L / L2);
+    const int64_t colbytes = L2 * dsize, rowbytes = padded(L1, dsize) * dsize;
+    const int wcap = (int)std::min<int64_t>(threads / pc.tpt, avail / ((1 + ks.nfwd) * colbytes));
+    const int ncap = (int)std::min<int64_t>(threads / pr.tpt, avail / (ks.narr * rowbytes));
+    if (wcap < 1 || ncap < 1) continue;
+    const int nr = largest_divisor_at_most((int)L2, ncap);
+    for (int wmax : {64, 32, 16, 8}) {
+      if (n >= maxn) break;
+      const int w = largest_divisor_at_most(L1, std::min(wcap, wmax));
+      bool dup = false;
+      for (int q = 0; q < n; ++q)
+        if (out[q].level == 2 && out[q].L2 == L2 && out[q].w == w) dup = true;
+      if (dup) continue;
+      CfgDev c{};
+      c.level = 2; c.m = (int32_t)m; c.L = (int32_t)L; c.TN = (int32_t)TN;
+      c.L1 = L1; c.L2 = (int32_t)L2; c.w = w; c.nr = nr; c.pr = pr; c.pc = pc; c.nt = 1;
+      c.smem = (int32_t)(rb + std::max<int64_t>((1 + ks.nfwd) * w * colbytes, ks.narr * nr * rowbytes));
+      out[n++] = c;
+    }
+  }
+  return n;
 }
 
 size_t cfg_scratch_bytes(int kind, const CfgDev& c, int dsize) {

@@ -47,7 +47,8 @@ struct CfgDev {
 
 struct Item { int32_t cfg, first, count, pad; };
 
-bool make_fft_plan(int L, int emax, FftPlan* out);
+bool make_fft_plan(int L, int emax, FftPlan* out);     // generic plan (axis passes)
+bool make_fused_plan(int L, int dsize, FftPlan* out);  // fused 1D engine
 int64_t fft_flops(int L);   // nominal 5 L log2 L
 
 // Chooses a configuration for size m of a kind; returns false when m is not
@@ -55,6 +56,11 @@ int64_t fft_flops(int L);   // nominal 5 L log2 L
 // When force_level is 1 or 2 it forces that path (fails if impossible).
 bool make_cfg(int kind, int64_t m, int dsize, int threads, int smem_max, int force_level,
               CfgDev* out);
+
+// Candidate configurations for the autotuner: the default first, then
+// level 1 with fewer instances per block and level 2 with other splits and
+// tile widths.  Returns the number written (<= maxn).
+int enumerate_cfgs(int kind, int64_t m, int dsize, int threads, int smem_max, CfgDev* out, int maxn);
 
 // Scratch bytes one block needs for a level-2 configuration.
 size_t cfg_scratch_bytes(int kind, const CfgDev& c, int dsize);
