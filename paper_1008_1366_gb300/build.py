@@ -16,7 +16,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdealias.so")
 
-SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu",
+           "fixed_batched.cu"]
 # the fused 1D kernel, one translation unit per (kind, precision)
 INSTANCES = [(k, tag, c) for k in range(6) for tag, c in (("f", "float2"), ("d", "double2"))]
 

@@ -1,5 +1,10 @@
 // Batched 1D complex convolutions of uneven sizes in one persistent launch.
 //
+// FP32 batches whose sizes all lie in the set {2^a, 3*2^a, 5*2^a} in
+// [64, 65536] run on the fixed-shape engine (fixed.cuh, fixed_batched.cu):
+// a task queue of level-1 groups and level-2 pass tasks.  Other batches
+// run on the runtime-shaped engine (conv1d.cuh), as follows.
+//
 // Planning groups the instances by size; each size gets a configuration
 // (level 1: `nt` instances per block wholly in shared memory; level 2: one
 // instance per block through a scratch slot).  With DC_PLAN_AUTOTUNE the
@@ -15,6 +20,7 @@
 #include <vector>
 
 #include "conv1d.cuh"
+#include "fixed.h"
 #include "launch.h"
 #include "plan.h"
 #include "tables.h"
@@ -34,6 +40,15 @@ struct dc_batched_plan {
   int64_t* d_off = nullptr;
   int grid = 0, smem = 0;
   size_t slot = 0, work = 0;
+  // fixed-shape engine
+  bool fx = false;
+  fx::HostPlan hp;
+  fx::Task* d_tasks = nullptr;
+  fx::L2Inst* d_l2 = nullptr;
+  const float2* tabs[fx::kNumSizes] = {};
+  size_t cnt_bytes = 0;   // header + counters, zeroed before each launch
+  int fx_target = 0;      // column tiles per level-2 batch
+  std::vector<int64_t> off_host;
 };
 
 namespace {
@@ -127,6 +142,129 @@ dc_status autotune_size(int64_t m, int count, int ds, int smem_max, CfgDev* best
   cudaGetLastError();
   return DC_OK;
 }
+size_t fx_work_bytes(const dc_batched_plan* p) {
+  return p->cnt_bytes + p->hp.scratch * sizeof(float2);
+}
+
+dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
+  if (p->dmem) { cudaFree(p->dmem); p->dmem = nullptr; }
+  const fx::HostPlan& hp = p->hp;
+  const size_t bt = align_up(std::max<size_t>(1, hp.tasks.size()) * sizeof(fx::Task), 256);
+  const size_t bl = align_up(std::max<size_t>(1, hp.l2.size()) * sizeof(fx::L2Inst), 256);
+  const size_t bo = align_up(std::max<size_t>(1, hp.order.size()) * sizeof(int32_t), 256);
+  const size_t bf = align_up(off.size() * sizeof(int64_t), 256);
+  DC_CUDA_TRY(cudaMalloc(&p->dmem, bt + bl + bo + bf));
+  p->d_tasks = (fx::Task*)p->dmem;
+  p->d_l2 = (fx::L2Inst*)(p->dmem + bt);
+  p->d_order = (int32_t*)(p->dmem + bt + bl);
+  p->d_off = (int64_t*)(p->dmem + bt + bl + bo);
+  if (!hp.tasks.empty())
+    DC_CUDA_TRY(cudaMemcpy(p->d_tasks, hp.tasks.data(), hp.tasks.size() * sizeof(fx::Task), cudaMemcpyHostToDevice));
+  if (!hp.l2.empty())
+    DC_CUDA_TRY(cudaMemcpy(p->d_l2, hp.l2.data(), hp.l2.size() * sizeof(fx::L2Inst), cudaMemcpyHostToDevice));
+  if (!hp.order.empty())
+    DC_CUDA_TRY(cudaMemcpy(p->d_order, hp.order.data(), hp.order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  DC_CUDA_TRY(cudaMemcpy(p->d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  p->cnt_bytes = align_up(sizeof(WorkHeader) + hp.ncnt * sizeof(uint32_t), 256);
+  p->work = fx_work_bytes(p);
+  return DC_OK;
+}
+
+dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work, cudaStream_t s) {
+  DC_CUDA_TRY(cudaMemsetAsync(work, 0, p->cnt_bytes, s));
+  fx::FxArgs a{};
+  a.f = (const float2*)f;
+  a.g = (const float2*)g;
+  a.h = (float2*)h;
+  a.off = p->d_off;
+  a.order = p->d_order;
+  a.tasks = p->d_tasks;
+  a.ntasks = (int32_t)p->hp.tasks.size();
+  a.l2 = p->d_l2;
+  a.hdr = (WorkHeader*)work;
+  a.cnt = (uint32_t*)((char*)work + sizeof(WorkHeader));
+  a.scratch = (float2*)((char*)work + p->cnt_bytes);
+  for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
+  return fx::launch(a, p->grid, p->smem, s);
+}
+
+// Times the whole batch on scratch buffers (median of three after a warm-up, ms).
+float fx_time(dc_batched_plan* p, const std::vector<int64_t>& off, cudaStream_t s) {
+  DevBuf f, g, h, w;
+  const size_t bytes = (size_t)p->total * sizeof(float2);
+  if (cudaMalloc(&f.p, bytes) != cudaSuccess || cudaMalloc(&g.p, bytes) != cudaSuccess ||
+      cudaMalloc(&h.p, bytes) != cudaSuccess || cudaMalloc(&w.p, p->work) != cudaSuccess)
+    return -1;
+  cudaMemset(f.p, 0x3c, bytes);
+  cudaMemset(g.p, 0x3b, bytes);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<float> t;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, s);
+    if (fx_launch(p, f.p, g.p, h.p, w.p, s) != DC_OK) break;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) t.push_back(ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int32_t st[2] = {0, 0};
+  cudaMemcpy(st, w.p, sizeof(st), cudaMemcpyDeviceToHost);
+  if (cudaGetLastError() != cudaSuccess || t.size() < 3 || st[0] != 0) return -1;
+  std::sort(t.begin(), t.end());
+  return t[1];
+}
+
+dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const std::vector<int64_t>& off,
+                       int32_t flags) {
+  p->fx = true;
+  p->off_host = off;
+  int bps = 0;
+  // kernel attributes for the largest shared-memory need of any size
+  int smem_all = 0;
+  for (int c = 0; c < fx::kNumSizes; ++c) smem_all = std::max(smem_all, fx::code_smem(c));
+  dc_status st = fx::prepare_kernel(smem_all, &bps);
+  if (st != DC_OK) return st;
+  p->grid = bps * device_info().sms;
+  int target = p->grid / 2;
+  if (!fx::build_plan(m, n, off.data(), target, &p->hp)) return DC_ERR_SIZE;
+  p->smem = p->hp.smem;
+  for (int c : p->hp.codes) {
+    const void* tw = nullptr;
+    st = get_root_table(2 * fx::code_size(c), 8, &tw);
+    if (st != DC_OK) return st;
+    p->tabs[c] = (const float2*)tw;
+  }
+  st = fx_upload(p, off);
+  if (st != DC_OK) return st;
+  if (flags & DC_PLAN_AUTOTUNE) {
+    // the pipeline distance between the level-2 passes: trades waiting
+    // against the scratch footprint in L2
+    cudaStream_t s;
+    DC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    int best = target;
+    float tbest = fx_time(p, off, s);
+    for (int cand : {p->grid / 4, p->grid, 2 * p->grid}) {
+      if (cand < 1 || !fx::build_plan(m, n, off.data(), cand, &p->hp)) continue;
+      if (fx_upload(p, off) != DC_OK) continue;
+      const float t = fx_time(p, off, s);
+      if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; best = cand; }
+    }
+    cudaStreamDestroy(s);
+    cudaGetLastError();
+    if (!fx::build_plan(m, n, off.data(), best, &p->hp)) return DC_ERR_SIZE;
+    st = fx_upload(p, off);
+    if (st != DC_OK) return st;
+    p->fx_target = best;
+  } else {
+    p->fx_target = target;
+  }
+  return DC_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -150,6 +288,15 @@ dc_status dc_batched_plan_create(const int64_t* m, int32_t n, int32_t dtype, int
     by_size[m[i]].push_back(i);
   }
   p->total = off[n];
+
+  bool all_fixed = ds == 8 && !one;
+  for (int32_t i = 0; i < n && all_fixed; ++i) all_fixed = fx::size_code(m[i]) >= 0;
+  if (all_fixed) {
+    dc_status st = create_fixed(p, m, n, off, flags);
+    if (st != DC_OK) { delete p; return st; }
+    *out = p;
+    return DC_OK;
+  }
 
   struct Pending { Item it; double cost; std::vector<int32_t> ids; };
   std::vector<Pending> pend;
@@ -225,12 +372,24 @@ dc_status dc_batched_plan_workspace_size(const dc_batched_plan* p, size_t* bytes
 
 dc_status dc_batched_plan_launches(const dc_batched_plan* p, int32_t* launches) {
   if (!p || !launches) return DC_ERR_ARG;
-  *launches = (p->flags & DC_PLAN_ONE_PER_LAUNCH) ? (int32_t)p->items.size() : 1;
+  *launches = (!p->fx && (p->flags & DC_PLAN_ONE_PER_LAUNCH)) ? (int32_t)p->items.size() : 1;
   return DC_OK;
 }
 
 dc_status dc_batched_plan_describe(const dc_batched_plan* p, int32_t i, int64_t* m, int32_t* level,
                                    int32_t* nt, int32_t* l1, int32_t* l2, int32_t* w) {
+  if (p && p->fx) {
+    if (i < 0 || i >= (int32_t)p->hp.codes.size()) return DC_ERR_ARG;
+    int lv, per, a, b, ww;
+    fx::code_shape(p->hp.codes[i], &lv, &per, &a, &b, &ww);
+    if (m) *m = fx::code_size(p->hp.codes[i]);
+    if (level) *level = lv;
+    if (nt) *nt = per;
+    if (l1) *l1 = a;
+    if (l2) *l2 = b;
+    if (w) *w = ww;
+    return DC_OK;
+  }
   if (!p || i < 0 || i >= (int32_t)p->cfgs.size()) return DC_ERR_ARG;
   const CfgDev& c = p->cfgs[i];
   if (m) *m = c.m;
@@ -258,6 +417,7 @@ dc_status dc_conv_complex_1d_batched(const dc_batched_plan* p, const void* f, co
   };
   if (overl(h, f) || overl(h, g)) return DC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->fx) return fx_launch(p, f, g, h, work, s);
   ConvArgs a{};
   a.in[0] = f;
   a.in[1] = g;

@@ -49,6 +49,21 @@ template <class C> struct RealOf;
 template <> struct RealOf<float2> { using type = float; };
 template <> struct RealOf<double2> { using type = double; };
 
+template <class C> struct Ctx {
+  const C* in0;     // inputs and outputs as named pointers: never indexed at
+  const C* in1;     // run time, so they stay in registers
+  const C* in2;
+  C* out0;
+  C* out1;
+  int m, TN;
+  Roots<C> rt;
+};
+
+// input x of an instance (x = 0, 1, 2)
+template <class C> __device__ __forceinline__ const C* in_ptr(const Ctx<C>& c, int x) {
+  return x == 0 ? c.in0 : (x == 1 ? c.in1 : c.in2);
+}
+
 // ---------------------------------------------------------------------------
 // kind policies: residue inputs, pointwise product, recombination, scaling
 // ---------------------------------------------------------------------------
@@ -57,8 +72,8 @@ template <int KIND, class C> struct KP;
 // complex binary convolution, N = 2m, residues r = 0, 1 (Eqs. (2.1)-(2.2))
 template <class C> struct KP<K_COMPLEX, C> {
   static constexpr int Q = 2, NARR = 2, NFWD = 1;
-  __device__ static C build(const C* const* in, int x, int k, int ri, int m, const Roots<C>& rt) {
-    C v = in[x][k];
+  __device__ static C build(const Ctx<C>& c, int x, int k, int ri, int m, const Roots<C>& rt) {
+    C v = in_ptr(c, x)[k];
     return ri ? cmul(v, rt.at(k)) : v;
   }
   __device__ static void pointwise(C* v) { v[0] = cmul(v[0], v[1]); }
@@ -106,10 +121,10 @@ template <class C> __device__ __forceinline__ C real_part(C a) { a.y = 0; return
 // transformed as a complex array with zero imaginary part.
 template <class C> struct KP<K_HERMITIAN, C> {
   static constexpr int Q = 3, NARR = 1, NFWD = 1;
-  __device__ static C build(const C* const* in, int, int k, int ri, int m, const Roots<C>& rt) {
+  __device__ static C build(const Ctx<C>& c, int, int k, int ri, int m, const Roots<C>& rt) {
     const int r = ri - 1;
-    return pack_i(herm_w(in[0], k, r, m, rt, real_part(in[0][0])),
-                  herm_w(in[1], k, r, m, rt, real_part(in[1][0])));
+    return pack_i(herm_w(c.in0, k, r, m, rt, real_part(c.in0[0])),
+                  herm_w(c.in1, k, r, m, rt, real_part(c.in1[0])));
   }
   __device__ static void pointwise(C* v) { v[0].x = v[0].x * v[0].y; v[0].y = 0; }
   __device__ static C contrib(int, C X, int k, int ri, int, const Roots<C>& rt) {
@@ -138,9 +153,9 @@ __device__ __forceinline__ C tern_v(const C* u, int k, int r, int m, const Roots
 // length 2m: (V^f + i V^g) and V^e backward, the triple real product forward.
 template <class C> struct KP<K_TERNARY, C> {
   static constexpr int Q = 2, NARR = 2, NFWD = 1;
-  __device__ static C build(const C* const* in, int x, int k, int ri, int m, const Roots<C>& rt) {
-    if (x == 0) return pack_i(tern_v(in[0], k, ri, m, rt), tern_v(in[1], k, ri, m, rt));
-    return tern_v(in[2], k, ri, m, rt);
+  __device__ static C build(const Ctx<C>& c, int x, int k, int ri, int m, const Roots<C>& rt) {
+    if (x == 0) return pack_i(tern_v(c.in0, k, ri, m, rt), tern_v(c.in1, k, ri, m, rt));
+    return tern_v(c.in2, k, ri, m, rt);
   }
   __device__ static void pointwise(C* v) { v[0].x = v[0].x * v[0].y * v[1].x; v[0].y = 0; }
   __device__ static C contrib(int, C X, int k, int ri, int, const Roots<C>& rt) {
@@ -157,8 +172,8 @@ template <class C> struct KP<K_TERNARY, C> {
 // W conj(F) -> dg are forward transformed (N = 2m correlation).
 template <class C> struct KP<K_COMPLEX_ADJ, C> {
   static constexpr int Q = 2, NARR = 3, NFWD = 2;
-  __device__ static C build(const C* const* in, int x, int k, int ri, int m, const Roots<C>& rt) {
-    return KP<K_COMPLEX, C>::build(in, x, k, ri, m, rt);
+  __device__ static C build(const Ctx<C>& c, int x, int k, int ri, int m, const Roots<C>& rt) {
+    return KP<K_COMPLEX, C>::build(c, x, k, ri, m, rt);
   }
   __device__ static void pointwise(C* v) {
     C a = cmulc(v[0], v[2]);
@@ -177,15 +192,15 @@ template <class C> struct KP<K_COMPLEX_ADJ, C> {
 // share the second transform; the two real products are forward transformed.
 template <class C> struct KP<K_HERMITIAN_ADJ, C> {
   static constexpr int Q = 3, NARR = 2, NFWD = 2;
-  __device__ static C build(const C* const* in, int x, int k, int ri, int m, const Roots<C>& rt) {
+  __device__ static C build(const Ctx<C>& c, int x, int k, int ri, int m, const Roots<C>& rt) {
     const int r = ri - 1;
     if (x == 0) {
-      C w0 = real_part(in[0][0]);
+      C w0 = real_part(c.in0[0]);
       w0.x *= 2;
-      return herm_w(in[0], k, r, m, rt, w0);
+      return herm_w(c.in0, k, r, m, rt, w0);
     }
-    return pack_i(herm_w(in[1], k, r, m, rt, real_part(in[1][0])),
-                  herm_w(in[2], k, r, m, rt, real_part(in[2][0])));
+    return pack_i(herm_w(c.in1, k, r, m, rt, real_part(c.in1[0])),
+                  herm_w(c.in2, k, r, m, rt, real_part(c.in2[0])));
   }
   __device__ static void pointwise(C* v) {
     const auto uw = v[0].x, uf = v[1].x, ug = v[1].y;
@@ -209,11 +224,11 @@ template <class C> struct KP<K_HERMITIAN_ADJ, C> {
 // done by the outer passes.
 template <class C> struct KP<K_HERMITIAN_PAIR, C> {
   static constexpr int Q = 3, NARR = 2, NFWD = 2;
-  __device__ static C build(const C* const* in, int x, int k, int ri, int m, const Roots<C>& rt) {
+  __device__ static C build(const Ctx<C>& c, int x, int k, int ri, int m, const Roots<C>& rt) {
     const int r = ri - 1;
-    if (x == 0) return herm_w(in[0], k, r, m, rt, real_part(in[0][0]));
-    return pack_i(herm_w(in[1], k, r, m, rt, real_part(in[1][0])),
-                  herm_w(in[2], k, r, m, rt, real_part(in[2][0])));
+    if (x == 0) return herm_w(c.in0, k, r, m, rt, real_part(c.in0[0]));
+    return pack_i(herm_w(c.in1, k, r, m, rt, real_part(c.in1[0])),
+                  herm_w(c.in2, k, r, m, rt, real_part(c.in2[0])));
   }
   __device__ static void pointwise(C* v) { KP<K_HERMITIAN_ADJ, C>::pointwise(v); }
   __device__ static C contrib(int o, C X, int k, int ri, int m, const Roots<C>& rt) {
@@ -251,13 +266,6 @@ template <class C> struct Dst {
   C* g;
   int64_t gb;
 };
-template <class C> struct Ctx {
-  const C* in[3];
-  C* out[2];
-  int m, TN;
-  Roots<C> rt;
-};
-
 template <class C> __device__ __forceinline__ Src<C> src_smem(Arr<C> a) {
   Src<C> s{}; s.mode = SRC_SMEM; s.a = a; return s;
 }
@@ -280,7 +288,7 @@ template <class C> __device__ __forceinline__ Dst<C> dst_sink(int o, int ri, int
 template <int KIND, class C>
 __device__ __forceinline__ C load_src(const Src<C>& s, const Ctx<C>& c, int idx) {
   if (s.mode == SRC_SMEM) return s.a[idx];
-  if (s.mode == SRC_BUILD) return KP<KIND, C>::build(c.in, s.x, s.kb + idx * s.ks, s.ri, c.m, c.rt);
+  if (s.mode == SRC_BUILD) return KP<KIND, C>::build(c, s.x, s.kb + idx * s.ks, s.ri, c.m, c.rt);
   return s.g[s.gb + (int64_t)idx * s.gs];
 }
 
@@ -298,79 +306,87 @@ __device__ __forceinline__ void store_dst(const Dst<C>& d, const Ctx<C>& c, int 
       const C cv = K::contrib(d.o, v, k, d.ri, c.m, c.rt);
       if (d.ri == 0) d.h[idx] = cv;
       else if (d.ri < K::Q - 1) d.h[idx] = cadd(d.h[idx], cv);
-      else c.out[d.o][k] = K::finish(d.o, cadd(d.h[idx], cv), k, c.m);
+      else (d.o == 0 ? c.out0 : c.out1)[k] = K::finish(d.o, cadd(d.h[idx], cv), k, c.m);
     }
   }
 }
 
-// one Stockham stage: gather x[j + q L/R] from src, twiddle + DFT, scatter
-// to (j - k) R + k + q Ns in dst.  sync_mid: barrier between gather and
-// scatter (in-place shared-memory stages).
+// one Stockham stage of radix RR: gather x[j + q L/RR] from src, twiddle +
+// DFT, scatter to (j - k) RR + k + q Ns in dst.  sync_mid: barrier between
+// gather and scatter (in-place shared-memory stages).  Plain parameters and
+// an explicit radix switch (no capturing lambdas) keep every local in
+// registers.
+template <int RR, int E, int KIND, int SM, int DM, class C>
+__device__ __forceinline__ void stage_r(int Ns, int L, int tpt, int sgn, Src<C> src, Dst<C> dst,
+                                        bool sync_mid, int i, bool act, const Ctx<C>& ctx) {
+  constexpr int NB = E / RR;
+  using K = KP<KIND, C>;
+  C v[E];
+  // the source / destination switch sits outside the unrolled loops
+  if (act) {
+    const int LR = L / RR;
+    if constexpr (SM == SRC_SMEM) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int q = 0; q < RR; ++q) v[b * RR + q] = src.a[i + b * tpt + q * LR];
+    } else if constexpr (SM == SRC_BUILD) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int q = 0; q < RR; ++q)
+          v[b * RR + q] = K::build(ctx, src.x, src.kb + (i + b * tpt + q * LR) * src.ks, src.ri,
+                                   ctx.m, ctx.rt);
+    } else {
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int q = 0; q < RR; ++q)
+          v[b * RR + q] = src.g[src.gb + (int64_t)(i + b * tpt + q * LR) * src.gs];
+    }
+  }
+  if (sync_mid) __syncthreads();
+  if (act) {
+    bfly<RR, NB>(v, i, tpt, Ns, ctx.TN / (Ns * RR), ctx.rt, sgn);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = i + b * tpt;
+      const int k = j & (Ns - 1);   // Ns is a power of two (odd radix last)
+      const int ob = (j - k) * RR + k;
+#pragma unroll
+      for (int q = 0; q < RR; ++q) {
+        const int idx = ob + q * Ns;
+        if constexpr (DM == DST_SMEM) {
+          dst.a[idx] = v[b * RR + q];
+        } else if constexpr (DM == DST_GTW) {
+          const C w = ctx.rt.at(idx * dst.twm);
+          dst.g[dst.gb + (int64_t)idx * dst.gs] = dst.tsgn > 0 ? cmul(v[b * RR + q], w) : cmulc(v[b * RR + q], w);
+        } else {
+          store_dst<KIND>(dst, ctx, idx, v[b * RR + q]);
+        }
+      }
+    }
+  }
+}
+
 template <int E, int KIND, int SM, int DM, class C>
-__device__ __forceinline__ void stage_body(int R, int Ns, int L, int tpt, int sgn, const Src<C>& src,
-                                           const Dst<C>& dst, bool sync_mid, int i, bool act,
+__device__ __forceinline__ void stage_body(int R, int Ns, int L, int tpt, int sgn, Src<C> src,
+                                           Dst<C> dst, bool sync_mid, int i, bool act,
                                            const Ctx<C>& ctx) {
-  with_radix<E>(R, [&](auto rc) {
-    constexpr int RR = decltype(rc)::value;
-    constexpr int NB = E / RR;
-    using K = KP<KIND, C>;
-    C v[E];
-    // the source / destination switch sits outside the unrolled loops, so
-    // each loop body stays simple and v stays in registers
-    if (act) {
-      const int LR = L / RR;
-      if constexpr (SM == SRC_SMEM) {
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-          for (int q = 0; q < RR; ++q) v[b * RR + q] = src.a[i + b * tpt + q * LR];
-      } else if constexpr (SM == SRC_BUILD) {
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-          for (int q = 0; q < RR; ++q)
-            v[b * RR + q] = K::build(ctx.in, src.x, src.kb + (i + b * tpt + q * LR) * src.ks, src.ri,
-                                     ctx.m, ctx.rt);
-      } else {
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-          for (int q = 0; q < RR; ++q)
-            v[b * RR + q] = src.g[src.gb + (int64_t)(i + b * tpt + q * LR) * src.gs];
-      }
-    }
-    if (sync_mid) __syncthreads();
-    if (act) {
-      bfly<RR, NB>(v, i, tpt, Ns, ctx.TN / (Ns * RR), ctx.rt, sgn);
-      int ob[NB];
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int j = i + b * tpt;
-        const int k = j % Ns;
-        ob[b] = (j - k) * RR + k;
-      }
-      if constexpr (DM == DST_SMEM) {
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-          for (int q = 0; q < RR; ++q) dst.a[ob[b] + q * Ns] = v[b * RR + q];
-      } else if constexpr (DM == DST_GTW) {
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-          for (int q = 0; q < RR; ++q) {
-            const int idx = ob[b] + q * Ns;
-            const C w = ctx.rt.at(idx * dst.twm);
-            dst.g[dst.gb + (int64_t)idx * dst.gs] = dst.tsgn > 0 ? cmul(v[b * RR + q], w) : cmulc(v[b * RR + q], w);
-          }
-      } else {
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-          for (int q = 0; q < RR; ++q) store_dst<KIND>(dst, ctx, ob[b] + q * Ns, v[b * RR + q]);
-      }
-    }
-  });
+  switch (R) {
+#define DC_STAGE_CASE(RV)                                                                              \
+    case RV:                                                                                           \
+      if constexpr (E % RV == 0) stage_r<RV, E, KIND, SM, DM>(Ns, L, tpt, sgn, src, dst, sync_mid, i, act, ctx); \
+      break;
+    DC_STAGE_CASE(2)
+    DC_STAGE_CASE(3)
+    DC_STAGE_CASE(4)
+    DC_STAGE_CASE(5)
+    DC_STAGE_CASE(8)
+    DC_STAGE_CASE(16)
+#undef DC_STAGE_CASE
+    default: break;
+  }
 }
 
 // The product stage: after the last backward stage (an ordinary in-place
@@ -379,45 +395,61 @@ __device__ __forceinline__ void stage_body(int R, int Ns, int L, int tpt, int sg
 // fly (only the NFWD products stay live), applies the first forward stage
 // (Ns = 1, no twiddles) and writes back in place.  Arrays A[x] = base +
 // x * astride, padded layout.
-template <int E, int KIND, class C>
-__device__ __forceinline__ void product_body(int R, int L, int tpt, C* base, int astride, int i, bool act,
-                                             const Ctx<C>& ctx) {
+template <int RR, int E, int KIND, class C>
+__device__ __forceinline__ void product_r(int L, int tpt, C* base, int astride, int i, bool act,
+                                          const Ctx<C>& ctx) {
   using K = KP<KIND, C>;
   constexpr int PS = pad_shift<C>();
-  with_radix<E>(R, [&](auto rc) {
-    constexpr int RR = decltype(rc)::value;
-    constexpr int NB = E / RR;
-    C v[K::NFWD][E];
-    if (act) {
-      const int LR = L / RR;
+  constexpr int NB = E / RR;
+  C v[K::NFWD][E];
+  if (act) {
+    const int LR = L / RR;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int q = 0; q < RR; ++q) {
+        const int idx = i + b * tpt + q * LR;
+        C w[K::NARR];
+#pragma unroll
+        for (int x = 0; x < K::NARR; ++x) w[x] = base[x * astride + idx + (idx >> PS)];
+        K::pointwise(w);
+#pragma unroll
+        for (int o = 0; o < K::NFWD; ++o) v[o][b * RR + q] = w[o];
+      }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int o = 0; o < K::NFWD; ++o) {
+      bfly<RR, NB>(v[o], i, tpt, 1, 1, ctx.rt, -1);
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
         for (int q = 0; q < RR; ++q) {
-          const int idx = i + b * tpt + q * LR;
-          C w[K::NARR];
-#pragma unroll
-          for (int x = 0; x < K::NARR; ++x) w[x] = base[x * astride + idx + (idx >> PS)];
-          K::pointwise(w);
-#pragma unroll
-          for (int o = 0; o < K::NFWD; ++o) v[o][b * RR + q] = w[o];
+          const int idx = (i + b * tpt) * RR + q;
+          base[o * astride + idx + (idx >> PS)] = v[o][b * RR + q];
         }
     }
-    __syncthreads();
-    if (act) {
-#pragma unroll
-      for (int o = 0; o < K::NFWD; ++o) {
-        bfly<RR, NB>(v[o], i, tpt, 1, 1, ctx.rt, -1);
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-          for (int q = 0; q < RR; ++q) {
-            const int idx = (i + b * tpt) * RR + q;
-            base[o * astride + idx + (idx >> PS)] = v[o][b * RR + q];
-          }
-      }
-    }
-  });
+  }
+}
+
+template <int E, int KIND, class C>
+__device__ __forceinline__ void product_body(int R, int L, int tpt, C* base, int astride, int i, bool act,
+                                             const Ctx<C>& ctx) {
+  switch (R) {
+#define DC_PROD_CASE(RV)                                                                   \
+    case RV:                                                                               \
+      if constexpr (E % RV == 0) product_r<RV, E, KIND>(L, tpt, base, astride, i, act, ctx); \
+      break;
+    DC_PROD_CASE(2)
+    DC_PROD_CASE(3)
+    DC_PROD_CASE(4)
+    DC_PROD_CASE(5)
+    DC_PROD_CASE(8)
+    DC_PROD_CASE(16)
+#undef DC_PROD_CASE
+    default: break;
+  }
 }
 
 // A phase of an item, from the thread's point of view:
@@ -473,7 +505,7 @@ __device__ __forceinline__ void run_phase(const Phase<C>& P, const CfgDev& cfg, 
   const FftPlan& p = *P.p;
   const int ns = p.ns, L = p.L, tpt = p.tpt;
   const bool one = P.type == PH_A || P.type == PH_C;
-  const bool rev = P.type == PH_C;
+  const bool fwd = P.type == PH_C;
   const int nb = K::NARR * ns;
   const int nops = one ? ns : nb + 1 + K::NFWD * (ns - 1);
   for (int op = 0; op < nops; ++op) {
@@ -481,11 +513,11 @@ __device__ __forceinline__ void run_phase(const Phase<C>& P, const CfgDev& cfg, 
     bool sync_mid = true, sync_after = true, first, last;
     if (one) {
       s = op;
-      R = p.r[rev ? ns - 1 - s : s];
-      for (int t = 0; t < s; ++t) Ns *= p.r[rev ? ns - 1 - t : t];
+      R = p.r[s];
+      for (int t = 0; t < s; ++t) Ns *= p.r[t];
       first = s == 0;
       last = s == ns - 1;
-      sgn = rev ? -1 : 1;
+      sgn = fwd ? -1 : 1;
     } else if (op < nb) {             // backward stages, stage-major: stage s of every array
       s = op / K::NARR;
       arr = op % K::NARR;
@@ -497,15 +529,15 @@ __device__ __forceinline__ void run_phase(const Phase<C>& P, const CfgDev& cfg, 
       sync_mid = s > 0;
       sync_after = s > 0 || arr == K::NARR - 1;
     } else if (op == nb) {            // product + first forward stage
-      product_body<E, KIND>(p.r[ns - 1], L, tpt, P.base, P.astride, P.i, P.act, ctx);
+      product_body<E, KIND>(p.r[0], L, tpt, P.base, P.astride, P.i, P.act, ctx);
       __syncthreads();
       continue;
-    } else {                          // forward stages of output arr (reversed radices)
+    } else {                          // forward stages 1.. of output arr (same radix order)
       const int o = op - nb - 1;
       arr = o / (ns - 1);
       s = o % (ns - 1) + 1;
-      R = p.r[ns - 1 - s];
-      for (int t = 0; t < s; ++t) Ns *= p.r[ns - 1 - t];
+      R = p.r[s];
+      for (int t = 0; t < s; ++t) Ns *= p.r[t];
       first = false;
       last = s == ns - 1;
       sync_mid = !last;
@@ -536,10 +568,11 @@ template <class C> __device__ __forceinline__ Ctx<C> inst_ctx(const ConvArgs& a,
   Ctx<C> c{};
   const int inst = a.order ? a.order[slot] : slot;
   const int64_t off = a.off ? a.off[inst] : (int64_t)inst * a.stride;
-#pragma unroll
-  for (int x = 0; x < 3; ++x) c.in[x] = a.in[x] ? (const C*)a.in[x] + off : nullptr;
-#pragma unroll
-  for (int o = 0; o < 2; ++o) c.out[o] = a.out[o] ? (C*)a.out[o] + off : nullptr;
+  c.in0 = a.in[0] ? (const C*)a.in[0] + off : nullptr;
+  c.in1 = a.in[1] ? (const C*)a.in[1] + off : nullptr;
+  c.in2 = a.in[2] ? (const C*)a.in[2] + off : nullptr;
+  c.out0 = a.out[0] ? (C*)a.out[0] + off : nullptr;
+  c.out1 = a.out[1] ? (C*)a.out[1] + off : nullptr;
   c.m = m;
   c.TN = TN;
   c.rt = rt;
@@ -561,7 +594,7 @@ __device__ void conv_level1_direct(const ConvArgs& a, const CfgDev& cfg, int fir
   C* base = sm + (size_t)(act ? t : 0) * (K::NARR * L + K::NFWD * m);
   for (int ri = 0; ri < K::Q; ++ri) {
     if (act)
-      for (int x = 0; x < K::NARR; ++x) base[x * L + i] = K::build(ctx.in, x, i, ri, m, rt);
+      for (int x = 0; x < K::NARR; ++x) base[x * L + i] = K::build(ctx, x, i, ri, m, rt);
     __syncthreads();
     C v[K::NARR];
     if (act) {

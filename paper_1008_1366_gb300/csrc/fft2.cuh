@@ -5,11 +5,10 @@
 // j = i + b*tpt (b < E/R) of each radix-R stage; it gathers inputs
 // x[j + q L/R], twiddles them by zeta_{Ns R}^{s q k} (k = j mod Ns, s = +1
 // backward, -1 forward), applies the radix-R DFT and scatters to
-// (j - k) R + k + q Ns.  Natural order in and out.  The backward transform
-// uses the plan's radices in order and the forward transform in reverse, so
-// the outputs a thread holds after the last backward stage (indices
-// j + q L/R) are exactly the inputs of its first forward stage, and the
-// pointwise product between them stays in registers.
+// (j - k) R + k + q Ns.  Natural order in and out.  Plans put the powers of
+// two first and the odd radix last, so every stage starts at a power-of-two
+// stride Ns (k is a mask, not a division); both directions use that order.
+// The pointwise product is fused into the first forward stage (conv1d.cuh).
 //
 // Roots of unity come from two short tables in shared memory,
 // zeta_TN^e = hi[e >> sh] * lo[e & mask], the factorization of Sec. 2.1 of
@@ -124,7 +123,7 @@ __device__ __forceinline__ void bfly(C* v, int i, int tpt, int Ns, int tstr, con
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if (Ns > 1) {
-      const int e = ((i + b * tpt) % Ns) * tstr;
+      const int e = ((i + b * tpt) & (Ns - 1)) * tstr;   // Ns is a power of two
 #pragma unroll
       for (int q = 1; q < R; ++q) {
         C w = rt.at(q * e);

@@ -1,0 +1,83 @@
+// Host interface of the fixed-shape FP32 complex engine (fixed.cuh,
+// fixed_batched.cu): task records, kernel arguments, planning, launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace dc {
+namespace fx {
+
+constexpr int kNumSizes = 31;   // {2^a, 3*2^a, 5*2^a} in [64, 65536]
+
+// task types of the persistent queue
+enum : int32_t { T_L1 = 0, T_A = 1, T_B = 2, T_C = 3 };
+
+// One queue entry.  kc = type << 8 | size code.  T_L1: a = first slot of
+// the order array, b = instance count.  T_A/T_B/T_C: a = level-2 instance,
+// b = column tile (A, C) or row group (B).  Before it starts the task waits
+// until cnt[widx] >= wneed (widx < 0: no wait); when done it adds one to
+// cnt[sidx] (sidx < 0: none).  Every wait names a counter that only tasks
+// earlier in the queue advance.
+struct Task {
+  int32_t kc, a, b, widx;
+  uint32_t wneed;
+  int32_t sidx;
+};
+
+struct L2Inst {
+  int64_t off;   // element offset of the instance in f, g, h
+  int64_t scr;   // element offset of its four m-element scratch arrays
+};
+
+struct FxArgs {
+  const float2* f;
+  const float2* g;
+  float2* h;
+  const int64_t* off;      // per-instance element offsets
+  const int32_t* order;    // instance ids of the level-1 tasks
+  const Task* tasks;
+  int32_t ntasks;
+  int32_t pad;
+  const L2Inst* l2;
+  uint32_t* cnt;           // dependency counters, zero before each launch
+  WorkHeader* hdr;         // status word and queue counter, zero before each launch
+  float2* scratch;
+  const float2* tab[kNumSizes];   // root tables zeta_{2m}^i, i < 2m, per size code
+};
+
+// size code of m, or -1 when m is not in the set
+int size_code(int64_t m);
+int64_t code_size(int code);
+bool code_level1(int code);
+// instances per task (level 1) or the level-2 split of a size code
+void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W);
+// dynamic shared memory the kernel needs for a size code
+int code_smem(int code);
+
+struct HostPlan {
+  std::vector<Task> tasks;
+  std::vector<L2Inst> l2;
+  std::vector<int32_t> order;
+  size_t ncnt = 0;          // dependency counters
+  size_t scratch = 0;       // scratch elements
+  int smem = 0;             // dynamic shared memory of the launch
+  std::vector<int> codes;   // distinct size codes of the plan
+};
+
+// Builds the task queue for n instances of sizes m[i] at element offsets
+// off[i] (all sizes must have a code).  batch_target: column tiles per
+// batch of level-2 instances (the pipeline distance between passes).
+bool build_plan(const int64_t* m, int32_t n, const int64_t* off, int batch_target, HostPlan* out);
+
+// kernel attributes, occupancy
+dc_status prepare_kernel(int smem, int* blocks_per_sm);
+dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s);
+
+}  // namespace fx
+}  // namespace dc

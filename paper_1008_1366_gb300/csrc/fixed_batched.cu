@@ -1,0 +1,465 @@
+// Persistent task-queue kernel of the fixed-shape FP32 complex engine and
+// its host-side planner.
+//
+// The queue holds level-1 tasks (a group of same-size instances wholly in
+// shared memory) and the three pass tasks of every level-2 instance (column
+// tiles of pass A, row groups of pass B, column tiles of pass C; fixed.cuh).
+// Blocks take tasks in queue order from an atomic counter.  A pass task
+// first waits until the pass it reads from is complete, which only tasks
+// earlier in the queue can bring about; every task taken is held by a
+// running block, so the earliest unfinished task never waits and the queue
+// always drains.  Every wait is bounded: past the limit the block records
+// DC_ERR_TIMEOUT in the status word and stops.
+//
+// Level-2 instances are processed in batches whose passes are staggered in
+// the queue (A of batch k, B of batch k-1, C of batch k-2, ...), so a pass
+// rarely waits; the scratch of a batch is one of four regions that stay
+// in L2, and a batch reuses its region after the batch four earlier has
+// finished pass C.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "fixed.cuh"
+#include "fixed.h"
+#include "launch.h"
+
+namespace dc {
+namespace fx {
+
+// size codes: 2^6..2^16, 3*2^5..3*2^14, 5*2^4..5*2^13
+__host__ __device__ constexpr int size_of_code(int c) {
+  return c < 11 ? (64 << c) : (c < 21 ? (96 << (c - 11)) : (80 << (c - 21)));
+}
+
+__host__ __device__ constexpr int ceil_log2(int x) {
+  int l = 0;
+  while ((1 << l) < x) ++l;
+  return l;
+}
+// split of the root table of zeta_TN into lo (2^sh entries) and hi
+__host__ __device__ constexpr int roots_sh(int TN) { return (ceil_log2(TN) + 1) / 2; }
+__host__ __device__ constexpr int roots_count(int TN) {
+  return (1 << roots_sh(TN)) + (TN + (1 << roots_sh(TN)) - 1) / (1 << roots_sh(TN));
+}
+static_assert(roots_count(131072) <= kRootsMax, "root table fits its reservation");
+static_assert(roots_count(98304) <= kRootsMax, "root table fits its reservation");
+static_assert(roots_count(81920) <= kRootsMax, "root table fits its reservation");
+
+template <int M> struct Shape {
+  static constexpr bool l1 = is_level1(M);
+  // level 1
+  static constexpr int E = family_E(M);
+  static constexpr int T = M / E;
+  static constexpr int G = l1 ? kThreads / T : 0;
+  // level 2 (placeholders for level-1 sizes)
+  static constexpr int L2 = l1 ? 128 : l2_cols(M);
+  static constexpr int L1 = l1 ? 128 : M / L2;
+  static constexpr int W = col_width(l1 ? 16384 : M);
+  static constexpr int E1 = family_E(L1);
+  static constexpr int T1 = L1 / E1;
+  static constexpr int GR = kThreads / T1;
+  static constexpr int nA = L1 / W;
+  static constexpr int nB = 2 * L2 / GR;
+  static constexpr int smem = l1 ? G * 2 * padded(M) * 8
+                                 : (GR * 2 * padded(L1) * 8 > W * L2 * 8 ? GR * 2 * padded(L1) * 8 : W * L2 * 8);
+};
+
+// ---------------------------------------------------------------------------
+// device side
+// ---------------------------------------------------------------------------
+
+// level 1: residue R of `count` instances of size M, one thread group each.
+// One function per residue: inlining both lets the compiler share index
+// arithmetic across them, which costs registers and spills.
+template <int M, int R>
+__device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C* sm, Roots<C> rt) {
+  using S = Shape<M>;
+  constexpr int E = S::E, T = S::T, PL = padded(M), TN = 2 * M;
+  const int gi = threadIdx.x / T, i = threadIdx.x % T;
+  const bool act = gi < count;
+  const int64_t off = act ? a->off[a->order[first + gi]] : 0;
+  const C* f = a->f + off;
+  const C* g = a->g + off;
+  C* h = a->h + off;
+  C* A = sm + gi * 2 * PL;
+  C* B = A + PL;
+  const float sc = 1.0f / (float)(2 * M);
+  // groups past `count` transform zeros and store nothing: the stages
+  // themselves carry no condition
+  const C zero = make_float2(0.f, 0.f);
+  if constexpr (R == 0) {
+    // residue 0 (Eq. (2.1) with r = 0): partial output
+    conv_residue<M, E, TN>(
+        i, true, A, B, rt, [&](int x, int arr) { return act ? __ldg((arr ? g : f) + x) : zero; },
+        [&](int x, int, C v) {
+          if (act) h[x] = cscale(v, sc);
+        });
+  } else {
+    // residue 1: inputs times zeta_{2m}^k, output times zeta_{2m}^{-k} (Eq. (2.2))
+    conv_residue<M, E, TN>(
+        i, true, A, B, rt,
+        [&](int x, int arr) { return act ? cmul(__ldg((arr ? g : f) + x), rt.at(x)) : zero; },
+        [&](int x, int, C v) {
+          if (act) h[x] = cadd(h[x], cscale(cmulc(v, rt.at(x)), sc));
+        });
+  }
+}
+
+// pass A: column tile `tile` of level-2 instance l
+template <int M>
+__device__ __forceinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, const Roots<C>& rt) {
+  using S = Shape<M>;
+  constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = kColE, TN = 2 * M;
+  using K = Stage<L2, E, 0, false>;
+  const int c = threadIdx.x % W, i = threadIdx.x / W;
+  const int k1 = tile * W + c;
+  const L2Inst in = a->l2[l];
+  C* scr = a->scratch + in.scr;
+#pragma unroll 1
+  for (int arr = 0; arr < 2; ++arr) {
+    const C* x = (arr ? a->g : a->f) + in.off + k1;
+    C raw[E];
+#pragma unroll
+    for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+      for (int q = 0; q < K::R; ++q) raw[b * K::R + q] = __ldg(x + L1 * pos<L2, E, 0, false>(i, b, q));
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+      C v[E];
+#pragma unroll
+      for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+        for (int q = 0; q < K::R; ++q) {
+          const int e = b * K::R + q;
+          v[e] = r ? cmul(raw[e], rt.at(k1 + L1 * pos<L2, E, 0, false>(i, b, q))) : raw[e];
+        }
+      C* dst = scr + (size_t)(2 * r + arr) * M + k1;
+      column<L2, E, W, TN, false>(v, i, sm + c, rt, [&](int j2, int, C y) {
+        __stcg(dst + (size_t)j2 * L1, cmul(y, rt.at(2 * j2 * k1)));
+      });
+      __syncthreads();
+    }
+  }
+}
+
+// pass B: row group `unit` (rows (r, j2), r = row / L2) of level-2 instance l
+template <int M>
+__device__ __forceinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, const Roots<C>& rt) {
+  using S = Shape<M>;
+  constexpr int L1 = S::L1, L2 = S::L2, E1 = S::E1, T1 = S::T1, GR = S::GR, PL = padded(L1), TN = 2 * M;
+  const int gi = threadIdx.x / T1, i = threadIdx.x % T1;
+  const int row = unit * GR + gi;
+  const int r = row / L2, j2 = row % L2;
+  C* scr = a->scratch + a->l2[l].scr;
+  C* sf = scr + (size_t)(2 * r) * M + (size_t)j2 * L1;
+  const C* sg = scr + (size_t)(2 * r + 1) * M + (size_t)j2 * L1;
+  C* A = sm + gi * 2 * PL;
+  C* B = A + PL;
+  conv_residue<L1, E1, TN>(
+      i, true, A, B, rt, [&](int x, int arr) { return __ldcg((arr ? sg : (const C*)sf) + x); },
+      [&](int x, int, C v) { __stcg(sf + x, cmulc(v, rt.at(2 * j2 * x))); });
+}
+
+// pass C: column tile `tile` of level-2 instance l, both residues, output
+template <int M>
+__device__ __forceinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, const Roots<C>& rt) {
+  using S = Shape<M>;
+  constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = kColE, TN = 2 * M;
+  using K = Stage<L2, E, 0, true>;
+  const int c = threadIdx.x % W, i = threadIdx.x / W;
+  const int k1 = tile * W + c;
+  const L2Inst in = a->l2[l];
+  const C* scr = a->scratch + in.scr;
+  C* h = a->h + in.off + k1;
+  const float sc = 1.0f / (float)(2 * M);
+  C y0[E];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const C* src = scr + (size_t)(2 * r) * M + k1;
+    C v[E];
+#pragma unroll
+    for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+      for (int q = 0; q < K::R; ++q) v[b * K::R + q] = __ldcg(src + (size_t)L1 * pos<L2, E, 0, true>(i, b, q));
+    if (r == 0) {
+      column<L2, E, W, TN, true>(v, i, sm + c, rt, [&](int, int e, C y) { y0[e] = y; });
+      __syncthreads();
+    } else {
+      column<L2, E, W, TN, true>(v, i, sm + c, rt, [&](int k2, int e, C y) {
+        const int k = k1 + L1 * k2;
+        h[(size_t)L1 * k2] = cscale(cadd(y0[e], cmulc(y, rt.at(k))), sc);
+      });
+    }
+  }
+}
+
+template <int M>
+__device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C* sm, Roots<C> rt) {
+  if constexpr (Shape<M>::l1) {
+    l1_residue<M, 0>(a, x, y, sm, rt);
+    __syncthreads();
+    l1_residue<M, 1>(a, x, y, sm, rt);
+  } else {
+    if (type == T_A) run_A<M>(a, x, y, sm, rt);
+    else if (type == T_B) run_B<M>(a, x, y, sm, rt);
+    else run_C<M>(a, x, y, sm, rt);
+  }
+}
+
+// bounded wait until *c >= need (thread 0 only); false on timeout
+__device__ __forceinline__ bool wait_geq(const uint32_t* c, uint32_t need) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    if (v >= need) return true;
+    if (clock64() - t0 > (1ll << 32)) return false;   // about two seconds
+    __nanosleep(256);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) fx_kernel(const __grid_constant__ FxArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* rts = (C*)smem_raw;
+  C* sm = rts + kRootsMax;
+  __shared__ Task s_task;
+  __shared__ int s_ok;
+  int cur = -1;
+  Roots<C> rt{rts, rts, 0, 0};
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const uint32_t idx = atomicAdd(&a.hdr->counter, 1u);
+      Task t;
+      t.kc = -1;
+      int ok = 1;
+      if (idx < (uint32_t)a.ntasks) {
+        t = a.tasks[idx];
+        if (t.widx >= 0 && !wait_geq(a.cnt + t.widx, t.wneed)) {
+          ok = 0;
+          record_error(a.hdr, DC_ERR_TIMEOUT, (int)idx);
+        }
+      }
+      s_task = t;
+      s_ok = ok;
+    }
+    __syncthreads();
+    const Task t = s_task;
+    if (t.kc < 0 || !s_ok) break;
+    const int code = t.kc & 255, type = t.kc >> 8;
+    if (code != cur) {
+      // lo = zeta_TN^b (b < 2^sh), hi = zeta_TN^(a 2^sh), from the full table
+      const int TN = 2 * size_of_code(code);
+      const int sh = roots_sh(TN), nlo = 1 << sh, cnt = roots_count(TN);
+      const C* tab = a.tab[code];
+      for (int e = threadIdx.x; e < cnt; e += kThreads) rts[e] = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
+      rt = Roots<C>{rts, rts + nlo, sh, nlo - 1};
+      cur = code;
+      __syncthreads();
+    }
+    switch (code) {
+#define DC_FX_CASE(c) \
+      case c: run_size<size_of_code(c)>(&a, type, t.a, t.b, sm, rt); break;
+      DC_FX_CASE(0) DC_FX_CASE(1) DC_FX_CASE(2) DC_FX_CASE(3) DC_FX_CASE(4) DC_FX_CASE(5)
+      DC_FX_CASE(6) DC_FX_CASE(7) DC_FX_CASE(8) DC_FX_CASE(9) DC_FX_CASE(10)
+      DC_FX_CASE(11) DC_FX_CASE(12) DC_FX_CASE(13) DC_FX_CASE(14) DC_FX_CASE(15)
+      DC_FX_CASE(16) DC_FX_CASE(17) DC_FX_CASE(18) DC_FX_CASE(19) DC_FX_CASE(20)
+      DC_FX_CASE(21) DC_FX_CASE(22) DC_FX_CASE(23) DC_FX_CASE(24) DC_FX_CASE(25)
+      DC_FX_CASE(26) DC_FX_CASE(27) DC_FX_CASE(28) DC_FX_CASE(29) DC_FX_CASE(30)
+#undef DC_FX_CASE
+      default: break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && t.sidx >= 0) {
+      __threadfence();
+      atomicAdd(a.cnt + t.sidx, 1u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+template <int... Cs> struct CodeTable {
+  static void fill(int* lvl, int* per, int* l1, int* l2, int* w, int* na, int* nb, int* smem) {
+    int k = 0;
+    ((lvl[k] = Shape<size_of_code(Cs)>::l1 ? 1 : 2, per[k] = Shape<size_of_code(Cs)>::G,
+      l1[k] = Shape<size_of_code(Cs)>::L1, l2[k] = Shape<size_of_code(Cs)>::L2, w[k] = Shape<size_of_code(Cs)>::W,
+      na[k] = Shape<size_of_code(Cs)>::nA, nb[k] = Shape<size_of_code(Cs)>::nB,
+      smem[k] = Shape<size_of_code(Cs)>::smem, ++k), ...);
+  }
+};
+struct Tables {
+  int lvl[kNumSizes], per[kNumSizes], l1[kNumSizes], l2[kNumSizes], w[kNumSizes], na[kNumSizes],
+      nb[kNumSizes], smem[kNumSizes];
+  Tables() {
+    CodeTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
+              26, 27, 28, 29, 30>::fill(lvl, per, l1, l2, w, na, nb, smem);
+  }
+};
+const Tables& tables() {
+  static Tables t;
+  return t;
+}
+}  // namespace
+
+int size_code(int64_t m) {
+  for (int c = 0; c < kNumSizes; ++c)
+    if (size_of_code(c) == m) return c;
+  return -1;
+}
+int64_t code_size(int code) { return size_of_code(code); }
+bool code_level1(int code) { return tables().lvl[code] == 1; }
+int code_smem(int code) { return tables().smem[code] + kRootsMax * 8; }
+void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W) {
+  const Tables& t = tables();
+  *level = t.lvl[code];
+  *per_task = t.lvl[code] == 1 ? t.per[code] : 1;
+  *L1 = t.lvl[code] == 1 ? 0 : t.l1[code];
+  *L2 = t.lvl[code] == 1 ? 0 : t.l2[code];
+  *W = t.lvl[code] == 1 ? 0 : t.w[code];
+}
+
+bool build_plan(const int64_t* m, int32_t n, const int64_t* off, int batch_target, HostPlan* out) {
+  const Tables& tb = tables();
+  HostPlan& P = *out;
+  P = HostPlan{};
+  std::map<int, std::vector<int32_t>> l1_by_code;
+  std::vector<std::pair<int, int32_t>> big;   // (code, instance)
+  std::vector<bool> used(kNumSizes, false);
+  for (int32_t i = 0; i < n; ++i) {
+    const int c = size_code(m[i]);
+    if (c < 0) return false;
+    used[c] = true;
+    if (tb.lvl[c] == 1) l1_by_code[c].push_back(i);
+    else big.push_back({c, i});
+  }
+  for (int c = 0; c < kNumSizes; ++c)
+    if (used[c]) {
+      P.codes.push_back(c);
+      P.smem = std::max(P.smem, code_smem(c));
+    }
+
+  // level-1 tasks, largest estimated cost first
+  struct L1T { double cost; int code; std::vector<int32_t> ids; };
+  std::vector<L1T> l1t;
+  for (auto& kv : l1_by_code) {
+    const int c = kv.first, per = tb.per[c];
+    const double ms = (double)size_of_code(c);
+    for (size_t s = 0; s < kv.second.size(); s += per) {
+      L1T t;
+      t.code = c;
+      t.ids.assign(kv.second.begin() + s, kv.second.begin() + std::min(kv.second.size(), s + per));
+      t.cost = (double)t.ids.size() * ms * (std::log2(ms) + 4.0);
+      l1t.push_back(std::move(t));
+    }
+  }
+  std::stable_sort(l1t.begin(), l1t.end(), [](const L1T& x, const L1T& y) { return x.cost > y.cost; });
+  std::vector<Task> l1tasks;
+  for (auto& t : l1t) {
+    Task k{(T_L1 << 8) | t.code, (int32_t)P.order.size(), (int32_t)t.ids.size(), -1, 0, -1};
+    P.order.insert(P.order.end(), t.ids.begin(), t.ids.end());
+    l1tasks.push_back(k);
+  }
+
+  // level-2 instances, largest first, in batches of about batch_target column tiles
+  std::stable_sort(big.begin(), big.end(), [](const std::pair<int, int32_t>& x, const std::pair<int, int32_t>& y) {
+    return size_of_code(x.first) > size_of_code(y.first);
+  });
+  const int n2 = (int)big.size();
+  std::vector<std::vector<int>> batches;
+  std::vector<int64_t> batch_elems;
+  {
+    int tiles = 0;
+    for (int l = 0; l < n2; ++l) {
+      if (batches.empty() || tiles >= std::max(1, batch_target)) {
+        batches.emplace_back();
+        batch_elems.push_back(0);
+        tiles = 0;
+      }
+      batches.back().push_back(l);
+      tiles += tb.na[big[l].first];
+    }
+  }
+  const int nbat = (int)batches.size();
+  int64_t region = 0;
+  for (int k = 0; k < nbat; ++k) {
+    int64_t s = 0;
+    for (int l : batches[k]) s += 4 * (int64_t)size_of_code(big[l].first);
+    region = std::max(region, s);
+  }
+  P.l2.resize(n2);
+  std::vector<uint32_t> batch_c(nbat, 0);
+  for (int k = 0; k < nbat; ++k) {
+    int64_t o = (int64_t)(k % 4) * region;
+    for (int l : batches[k]) {
+      const int c = big[l].first;
+      P.l2[l].off = off[big[l].second];
+      P.l2[l].scr = o;
+      o += 4 * (int64_t)size_of_code(c);
+      batch_c[k] += (uint32_t)tb.na[c];
+    }
+  }
+  P.scratch = (size_t)(nbat ? std::min(nbat, 4) : 0) * (size_t)region;
+  P.ncnt = (size_t)2 * n2 + nbat;
+  auto emit = [&](int type, int k) {
+    for (int l : batches[k]) {
+      const int c = big[l].first;
+      const int cnt = type == T_B ? tb.nb[c] : tb.na[c];
+      for (int u = 0; u < cnt; ++u) {
+        Task t{(type << 8) | c, l, u, -1, 0, -1};
+        if (type == T_A) {
+          if (k >= 4) { t.widx = 2 * n2 + (k - 4); t.wneed = batch_c[k - 4]; }
+          t.sidx = 2 * l;
+        } else if (type == T_B) {
+          t.widx = 2 * l; t.wneed = (uint32_t)tb.na[c]; t.sidx = 2 * l + 1;
+        } else {
+          t.widx = 2 * l + 1; t.wneed = (uint32_t)tb.nb[c]; t.sidx = 2 * n2 + k;
+        }
+        P.tasks.push_back(t);
+      }
+    }
+  };
+  for (int s = 0; s < nbat; ++s) {
+    emit(T_A, s);
+    if (s >= 1) emit(T_B, s - 1);
+    if (s >= 2) emit(T_C, s - 2);
+  }
+  // drain the pipeline with level-1 work between the last passes
+  size_t li = 0;
+  const size_t chunk = std::max<size_t>(1, (size_t)std::max(1, batch_target) * 2);
+  auto take_l1 = [&](size_t k) {
+    for (size_t e = 0; e < k && li < l1tasks.size(); ++e) P.tasks.push_back(l1tasks[li++]);
+  };
+  if (nbat >= 1) {
+    take_l1(chunk);
+    emit(T_B, nbat - 1);
+    if (nbat >= 2) emit(T_C, nbat - 2);
+    take_l1(chunk);
+    emit(T_C, nbat - 1);
+  }
+  take_l1(l1tasks.size());
+  return true;
+}
+
+dc_status prepare_kernel(int smem, int* blocks_per_sm) {
+  DC_CUDA_TRY(cudaFuncSetAttribute(fx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int b = 0;
+  DC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fx_kernel, kThreads, smem));
+  if (b < 1) return DC_ERR_SIZE;
+  *blocks_per_sm = b;
+  return DC_OK;
+}
+
+dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s) {
+  fx_kernel<<<grid, kThreads, smem, s>>>(a);
+  DC_CUDA_TRY(cudaGetLastError());
+  return DC_OK;
+}
+
+}  // namespace fx
+}  // namespace dc

@@ -111,14 +111,16 @@ bool make_fused_plan(int L, int dsize, FftPlan* out) {
     *out = p;
     return true;
   }
+  // powers of two first, the odd radix last: every stage then starts at a
+  // power-of-two stride Ns, and the forward transform uses the same order
   int ns = 0;
-  if (c) p.r[ns++] = 5;
-  if (b) p.r[ns++] = 3;
   int lg = 0;
   while ((1 << (lg + 1)) <= pmax) ++lg;
   int rem = a;
   while (rem >= lg) { p.r[ns++] = (int8_t)(1 << lg); rem -= lg; }
   if (rem > 0) p.r[ns++] = (int8_t)(1 << rem);
+  if (b) p.r[ns++] = 3;
+  if (c) p.r[ns++] = 5;
   if (ns > kMaxStages) return false;
   if (ns == 1) {          // one stage: the DFT by definition is as cheap
     p.E = 0;

@@ -1,0 +1,119 @@
+"""GPU parity of the fixed-shape FP32 engine (batched plans whose sizes all lie
+in {2^a, 3*2^a, 5*2^a}, 64 <= m <= 65536) against the FP64 oracle, through
+the C ABI.
+
+Covers every size of the set (both levels, every radix), partial level-1
+groups, level-2 instances spread over more batches than there are scratch
+regions (so regions are reused behind the dependency counters), the
+pipeline-distance settings the autotuner picks from, and the status word
+after each launch.  Bar: relative L2 <= 5e-7 log2(2m) per instance."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from conftest import fp32_tol, rel_l2
+from paper_1008_1366_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dc():
+    import paper_1008_1366_gb300 as dc
+    return dc
+
+
+def run_plan(dc, sizes, seed, flags=0):
+    f, g, off = synthetic.batched_inputs(sizes, seed)
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex64, flags=flags)
+    tf = torch.tensor(f, dtype=torch.complex64, device="cuda")
+    tg = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    work = plan.workspace(tf.device)
+    h = plan(tf, tg, work=work)
+    torch.cuda.synchronize()
+    assert dc.read_status(work) == (0, 0)
+    return plan, f, g, off, h.cpu().numpy()
+
+
+def check_all(sizes, f, g, off, h):
+    worst = 0.0
+    for i, m in enumerate(sizes):
+        a, b = off[i], off[i + 1]
+        ref = oracle.padded_complex(f[a:b], g[a:b])
+        e = rel_l2(h[a:b], ref)
+        worst = max(worst, e / fp32_tol(2 * m))
+        assert e <= fp32_tol(2 * m), (i, m, e)
+    return worst
+
+
+def test_every_size_once(dc):
+    sizes = list(synthetic.SIZES_31)
+    plan, f, g, off, h = run_plan(dc, sizes, 21)
+    assert plan.launches == 1
+    desc = plan.describe()
+    assert sorted(d[0] for d in desc) == sorted(sizes)
+    levels = {d[0]: d[1] for d in desc}
+    assert levels[8192] == 1 and levels[12288] == 1 and levels[10240] == 1
+    assert levels[16384] == 2 and levels[65536] == 2 and levels[20480] == 2 and levels[24576] == 2
+    check_all(sizes, f, g, off, h)
+
+
+def test_partial_groups_and_order(dc):
+    # level-1 groups that are full, partial and single; sizes interleaved
+    sizes = [64] * 130 + [96] * 3 + [4096] * 3 + [80, 160, 320] * 5 + [8192, 12288, 10240] * 2
+    rng = np.random.default_rng(3)
+    sizes = [sizes[i] for i in rng.permutation(len(sizes))]
+    _, f, g, off, h = run_plan(dc, sizes, 22)
+    check_all(sizes, f, g, off, h)
+
+
+def test_level2_region_reuse(dc):
+    # many level-2 instances: more batches than the four scratch regions
+    sizes = [65536] * 24 + [16384] * 30 + [49152] * 6 + [20480] * 8 + [2048] * 20
+    rng = np.random.default_rng(4)
+    sizes = [sizes[i] for i in rng.permutation(len(sizes))]
+    _, f, g, off, h = run_plan(dc, sizes, 23)
+    check_all(sizes, f, g, off, h)
+
+
+def test_autotuned_plan_matches(dc):
+    sizes = [65536] * 6 + [40960] * 4 + [640] * 40 + [24576] * 4
+    plan, f, g, off, h = run_plan(dc, sizes, 24, flags=1)
+    check_all(sizes, f, g, off, h)
+
+
+def test_repeat_launch_same_result(dc):
+    # counters and the queue are reset per launch: a second launch on the
+    # same workspace reproduces the first bit for bit
+    sizes = [32768] * 5 + [1536] * 9 + [5120] * 3
+    f, g, off = synthetic.batched_inputs(sizes, 25)
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex64)
+    tf = torch.tensor(f, dtype=torch.complex64, device="cuda")
+    tg = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    work = plan.workspace(tf.device)
+    h1 = plan(tf, tg, work=work).clone()
+    h2 = plan(tf, tg, work=work)
+    torch.cuda.synchronize()
+    assert torch.equal(h1, h2)
+    check_all(sizes, f, g, off, h2.cpu().numpy())
+
+
+def test_special_inputs(dc):
+    # delta inputs: f = e_0 gives h = g exactly up to rounding
+    sizes = [64, 12288, 65536]
+    total = sum(sizes)
+    rng = np.random.default_rng(7)
+    g = (rng.uniform(-1, 1, total) + 1j * rng.uniform(-1, 1, total))
+    f = np.zeros(total, dtype=np.complex128)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for i in range(len(sizes)):
+        f[off[i]] = 1.0
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex64)
+    tf = torch.tensor(f, dtype=torch.complex64, device="cuda")
+    tg = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    h = plan(tf, tg).cpu().numpy()
+    for i, m in enumerate(sizes):
+        a, b = off[i], off[i + 1]
+        assert rel_l2(h[a:b], g[a:b]) <= fp32_tol(2 * m)
