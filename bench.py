@@ -446,7 +446,7 @@ def main():
     peak, peak_kind = measured_peak_hbm()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": committed_traffic(alg_bytes), "peak_source": peak_kind,
-            "kernel": "conv1d_kernel<K_COMPLEX,float2> (persistent)",
+            "kernel": "dc::fx::fx_kernel (persistent task queue)",
             "alg_bytes_per_launch": alg_bytes}
     if rank == 0:
         line = {

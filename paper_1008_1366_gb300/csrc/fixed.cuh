@@ -83,8 +83,12 @@ __host__ __device__ constexpr int family_E(int L) {
 __host__ __device__ constexpr bool is_level1(int m) { return m <= kThreads * family_E(m); }
 __host__ __device__ constexpr int l2_cols(int m) { return m <= 32768 ? 128 : 256; }   // L2
 __host__ __device__ constexpr int l2_rows(int m) { return m / l2_cols(m); }           // L1
-constexpr int kColE = 8;                                                              // column E
-__host__ __device__ constexpr int col_width(int m) { return kThreads * kColE / l2_cols(m); }  // W
+// column transforms: 16 elements per thread where the tile width divides
+// the row length, else 8; tile width W = columns per 512-thread tile
+__host__ __device__ constexpr int col_E(int m) {
+  return l2_rows(m) % (kThreads * 16 / l2_cols(m)) == 0 ? 16 : 8;
+}
+__host__ __device__ constexpr int col_width(int m) { return kThreads * col_E(m) / l2_cols(m); }
 __host__ __device__ constexpr int padded(int L) { return (L + (L >> 4) + 2) & ~1; }
 
 template <int L, int E> struct Fft {
@@ -148,8 +152,36 @@ __device__ __forceinline__ void scatter(const C* v, int i, const Lay& X) {
   }
 }
 
-// twiddles zeta_{Ns R}^{+-q k} (from the root table of zeta_TN) and the
-// radix-R DFT of each butterfly; backward: +, forward: -
+// Powers w[q] = w1^q, q < R, of a stage twiddle from exact table values of
+// w1 and (R >= 8) w4 by products of depth at most three:
+// w2 = w1^2, w3 = w2 w1, w8 = w4^2, w_{4a+b} = w_{4a} w_b.  Two table
+// lookups per butterfly instead of R - 1.
+template <int R>
+__device__ __forceinline__ void tw_powers(C* w, C w1, C w4) {
+  w[1] = w1;
+  if constexpr (R > 2) w[2] = cmul(w1, w1);
+  if constexpr (R > 3) w[3] = cmul(w[2], w1);
+  if constexpr (R == 5) w[4] = cmul(w[2], w[2]);
+  if constexpr (R >= 8) {
+    w[4] = w4;
+#pragma unroll
+    for (int b = 1; b < 4; ++b) w[4 + b] = cmul(w4, w[b]);
+  }
+  if constexpr (R == 16) {
+    const C w8 = cmul(w4, w4);
+    const C w12 = cmul(w8, w4);
+    w[8] = w8;
+    w[12] = w12;
+#pragma unroll
+    for (int b = 1; b < 4; ++b) {
+      w[8 + b] = cmul(w8, w[b]);
+      w[12 + b] = cmul(w12, w[b]);
+    }
+  }
+}
+
+// twiddles zeta_{Ns R}^{+-q k} (root table of zeta_TN) and the radix-R DFT
+// of each butterfly; backward: +, forward: -
 template <int L, int E, int S, bool FWD, int TN>
 __device__ __forceinline__ void dft(C* v, int i, const Roots<C>& rt) {
   using K = Stage<L, E, S, FWD>;
@@ -160,11 +192,11 @@ __device__ __forceinline__ void dft(C* v, int i, const Roots<C>& rt) {
       static_assert(TN % (K::Ns * K::R) == 0, "root table must cover the stage");
       const int j = i + b * K::T;
       const int e = (j % K::Ns) * (TN / (K::Ns * K::R));
+      C w[K::R];
+      tw_powers<K::R>(w, rt.at(e), K::R >= 8 ? rt.at(4 * e) : rt.at(0));
 #pragma unroll
-      for (int q = 1; q < K::R; ++q) {
-        const C w = rt.at(q * e);
-        v[b * K::R + q] = FWD ? cmulc(v[b * K::R + q], w) : cmul(v[b * K::R + q], w);
-      }
+      for (int q = 1; q < K::R; ++q)
+        v[b * K::R + q] = FWD ? cmulc(v[b * K::R + q], w[q]) : cmul(v[b * K::R + q], w[q]);
     }
     rdft<K::R>(&v[b * K::R], sgn);
   }
@@ -179,8 +211,8 @@ __device__ __forceinline__ int pos(int i, int b, int q) {
 
 // ---------------------------------------------------------------------------
 // one residue of a convolution of length L on a thread group (level 1 and
-// the rows of pass B).  ld(x, arr) gives input arr (0: f, 1: g) at natural
-// index x, already twiddled for the residue; st(x, v) takes the forward
+// the rows of pass B).  ld(x, arr, e) gives input arr (0: f, 1: g) at natural
+// index x (register e), already twiddled for the residue; arr 0 comes first; st(x, v) takes the forward
 // transform's output at natural index x (e: its register index).  A and B: padded shared arrays of
 // the group.  Every thread of the block calls this (barriers inside).
 // ---------------------------------------------------------------------------
@@ -237,7 +269,7 @@ __device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, cons
 #pragma unroll
       for (int b = 0; b < K::NB; ++b)
 #pragma unroll
-        for (int q = 0; q < K::R; ++q) v[b * K::R + q] = ld(pos<L, E, 0, false>(i, b, q), arr);
+        for (int q = 0; q < K::R; ++q) v[b * K::R + q] = ld(pos<L, E, 0, false>(i, b, q), arr, b * K::R + q);
       dft<L, E, 0, false, TN>(v, i, rt);
       scatter<L, E, 0, false>(v, i, arr ? B : A);
     }

@@ -4,11 +4,12 @@
 // The queue holds level-1 tasks (a group of same-size instances wholly in
 // shared memory) and the three pass tasks of every level-2 instance (column
 // tiles of pass A, row groups of pass B, column tiles of pass C; fixed.cuh).
-// Blocks take tasks in queue order from an atomic counter.  A pass task
+// Blocks take tasks in queue order from an atomic counter (each block
+// holds the index of its next task while it runs the current one).  A pass task
 // first waits until the pass it reads from is complete, which only tasks
-// earlier in the queue can bring about; every task taken is held by a
-// running block, so the earliest unfinished task never waits and the queue
-// always drains.  Every wait is bounded: past the limit the block records
+// earlier in the queue can bring about.  The earliest unfinished task waits
+// on nothing, and the block holding it either runs it or runs an earlier
+// task, which is finished by the same argument, so the queue always drains.  Every wait is bounded: past the limit the block records
 // DC_ERR_TIMEOUT in the status word and stops.
 //
 // Level-2 instances are processed in batches whose passes are staggered in
@@ -63,6 +64,9 @@ template <int M> struct Shape {
   static constexpr int GR = kThreads / T1;
   static constexpr int nA = L1 / W;
   static constexpr int nB = 2 * L2 / GR;
+  static constexpr int EC = l1 ? 16 : col_E(M);
+  static_assert(l1 || (L1 % W == 0 && (2 * L2) % GR == 0 && L1 * L2 == M), "level-2 tiling must be exact");
+  static_assert(!l1 || kThreads % T == 0, "level-1 groups must tile the block");
   static constexpr int smem = l1 ? G * 2 * padded(M) * 8
                                  : (GR * 2 * padded(L1) * 8 > W * L2 * 8 ? GR * 2 * padded(L1) * 8 : W * L2 * 8);
 };
@@ -93,15 +97,20 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
   if constexpr (R == 0) {
     // residue 0 (Eq. (2.1) with r = 0): partial output
     conv_residue<M, E, TN>(
-        i, true, A, B, rt, [&](int x, int arr) { return act ? __ldg((arr ? g : f) + x) : zero; },
+        i, true, A, B, rt, [&](int x, int arr, int) { return act ? __ldg((arr ? g : f) + x) : zero; },
         [&](int x, int, C v) {
           if (act) h[x] = cscale(v, sc);
         });
   } else {
-    // residue 1: inputs times zeta_{2m}^k, output times zeta_{2m}^{-k} (Eq. (2.2))
+    // residue 1: inputs times zeta_{2m}^k (looked up once for f and g),
+    // output times zeta_{2m}^{-k} (Eq. (2.2))
+    C tw[E];
     conv_residue<M, E, TN>(
         i, true, A, B, rt,
-        [&](int x, int arr) { return act ? cmul(__ldg((arr ? g : f) + x), rt.at(x)) : zero; },
+        [&](int x, int arr, int e) {
+          if (arr == 0) tw[e] = rt.at(x);
+          return act ? cmul(__ldg((arr ? g : f) + x), tw[e]) : zero;
+        },
         [&](int x, int, C v) {
           if (act) h[x] = cadd(h[x], cscale(cmulc(v, rt.at(x)), sc));
         });
@@ -112,20 +121,25 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
 template <int M>
 __device__ __forceinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, const Roots<C>& rt) {
   using S = Shape<M>;
-  constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = kColE, TN = 2 * M;
+  constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 2 * M;
   using K = Stage<L2, E, 0, false>;
   const int c = threadIdx.x % W, i = threadIdx.x / W;
   const int k1 = tile * W + c;
   const L2Inst in = a->l2[l];
   C* scr = a->scratch + in.scr;
-#pragma unroll 1
+  // both inputs' columns are loaded before any transform (their latency
+  // overlaps the first transforms)
+  C raw[2][E];
+#pragma unroll
   for (int arr = 0; arr < 2; ++arr) {
     const C* x = (arr ? a->g : a->f) + in.off + k1;
-    C raw[E];
 #pragma unroll
     for (int b = 0; b < K::NB; ++b)
 #pragma unroll
-      for (int q = 0; q < K::R; ++q) raw[b * K::R + q] = __ldg(x + L1 * pos<L2, E, 0, false>(i, b, q));
+      for (int q = 0; q < K::R; ++q) raw[arr][b * K::R + q] = __ldg(x + L1 * pos<L2, E, 0, false>(i, b, q));
+  }
+#pragma unroll
+  for (int arr = 0; arr < 2; ++arr) {
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
       C v[E];
@@ -134,7 +148,7 @@ __device__ __forceinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, c
 #pragma unroll
         for (int q = 0; q < K::R; ++q) {
           const int e = b * K::R + q;
-          v[e] = r ? cmul(raw[e], rt.at(k1 + L1 * pos<L2, E, 0, false>(i, b, q))) : raw[e];
+          v[e] = r ? cmul(raw[arr][e], rt.at(k1 + L1 * pos<L2, E, 0, false>(i, b, q))) : raw[arr][e];
         }
       C* dst = scr + (size_t)(2 * r + arr) * M + k1;
       column<L2, E, W, TN, false>(v, i, sm + c, rt, [&](int j2, int, C y) {
@@ -159,7 +173,7 @@ __device__ __forceinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, c
   C* A = sm + gi * 2 * PL;
   C* B = A + PL;
   conv_residue<L1, E1, TN>(
-      i, true, A, B, rt, [&](int x, int arr) { return __ldcg((arr ? sg : (const C*)sf) + x); },
+      i, true, A, B, rt, [&](int x, int arr, int) { return __ldcg((arr ? sg : (const C*)sf) + x); },
       [&](int x, int, C v) { __stcg(sf + x, cmulc(v, rt.at(2 * j2 * x))); });
 }
 
@@ -167,7 +181,7 @@ __device__ __forceinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, c
 template <int M>
 __device__ __forceinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, const Roots<C>& rt) {
   using S = Shape<M>;
-  constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = kColE, TN = 2 * M;
+  constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 2 * M;
   using K = Stage<L2, E, 0, true>;
   const int c = threadIdx.x % W, i = threadIdx.x / W;
   const int k1 = tile * W + c;
@@ -176,24 +190,21 @@ __device__ __forceinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, c
   C* h = a->h + in.off + k1;
   const float sc = 1.0f / (float)(2 * M);
   C y0[E];
+  C vin[2][E];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const C* src = scr + (size_t)(2 * r) * M + k1;
-    C v[E];
 #pragma unroll
     for (int b = 0; b < K::NB; ++b)
 #pragma unroll
-      for (int q = 0; q < K::R; ++q) v[b * K::R + q] = __ldcg(src + (size_t)L1 * pos<L2, E, 0, true>(i, b, q));
-    if (r == 0) {
-      column<L2, E, W, TN, true>(v, i, sm + c, rt, [&](int, int e, C y) { y0[e] = y; });
-      __syncthreads();
-    } else {
-      column<L2, E, W, TN, true>(v, i, sm + c, rt, [&](int k2, int e, C y) {
-        const int k = k1 + L1 * k2;
-        h[(size_t)L1 * k2] = cscale(cadd(y0[e], cmulc(y, rt.at(k))), sc);
-      });
-    }
+      for (int q = 0; q < K::R; ++q) vin[r][b * K::R + q] = __ldcg(src + (size_t)L1 * pos<L2, E, 0, true>(i, b, q));
   }
+  column<L2, E, W, TN, true>(vin[0], i, sm + c, rt, [&](int, int e, C y) { y0[e] = y; });
+  __syncthreads();
+  column<L2, E, W, TN, true>(vin[1], i, sm + c, rt, [&](int k2, int e, C y) {
+    const int k = k1 + L1 * k2;
+    h[(size_t)L1 * k2] = cscale(cadd(y0[e], cmulc(y, rt.at(k))), sc);
+  });
 }
 
 template <int M>
@@ -229,15 +240,19 @@ __global__ void __launch_bounds__(kThreads, 1) fx_kernel(const __grid_constant__
   __shared__ int s_ok;
   int cur = -1;
   Roots<C> rt{rts, rts, 0, 0};
+  // thread 0 takes the next queue index while the current task runs
+  uint32_t next = 0;
+  if (threadIdx.x == 0) next = atomicAdd(&a.hdr->counter, 1u);
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      const uint32_t idx = atomicAdd(&a.hdr->counter, 1u);
+      const uint32_t idx = next;
       Task t;
       t.kc = -1;
       int ok = 1;
       if (idx < (uint32_t)a.ntasks) {
         t = a.tasks[idx];
+        next = atomicAdd(&a.hdr->counter, 1u);
         if (t.widx >= 0 && !wait_geq(a.cnt + t.widx, t.wneed)) {
           ok = 0;
           record_error(a.hdr, DC_ERR_TIMEOUT, (int)idx);
