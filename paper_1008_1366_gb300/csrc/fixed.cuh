@@ -14,7 +14,7 @@
 // pointwise product, one forward m-point transform, and the twiddled
 // accumulation into the output.
 //
-// Level 1 (m <= 512 E): one thread group of T = m/E threads per instance,
+// Level 1 (m <= 256 E): one thread group of T = m/E threads per instance,
 // both arrays in shared memory.  Stockham stages with natural order in and
 // out; the forward transform uses the backward radices in reverse order, so
 // the last backward stage and the first forward stage touch the same
@@ -41,7 +41,7 @@
 namespace dc {
 namespace fx {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 256;       // threads per block; two blocks per SM
 constexpr int kRootsMax = 768;   // shared-memory root entries reserved (2m <= 131072)
 
 using C = float2;
@@ -84,7 +84,7 @@ __host__ __device__ constexpr bool is_level1(int m) { return m <= kThreads * fam
 __host__ __device__ constexpr int l2_cols(int m) { return m <= 32768 ? 128 : 256; }   // L2
 __host__ __device__ constexpr int l2_rows(int m) { return m / l2_cols(m); }           // L1
 // column transforms: 16 elements per thread where the tile width divides
-// the row length, else 8; tile width W = columns per 512-thread tile
+// the row length, else 8; tile width W = columns per block-wide tile
 __host__ __device__ constexpr int col_E(int m) {
   return l2_rows(m) % (kThreads * 16 / l2_cols(m)) == 0 ? 16 : 8;
 }

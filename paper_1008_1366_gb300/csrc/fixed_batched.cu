@@ -232,7 +232,7 @@ __device__ __forceinline__ bool wait_geq(const uint32_t* c, uint32_t need) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) fx_kernel(const __grid_constant__ FxArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) fx_kernel(const __grid_constant__ FxArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* rts = (C*)smem_raw;
   C* sm = rts + kRootsMax;

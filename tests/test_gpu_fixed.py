@@ -55,8 +55,13 @@ def test_every_size_once(dc):
     desc = plan.describe()
     assert sorted(d[0] for d in desc) == sorted(sizes)
     levels = {d[0]: d[1] for d in desc}
-    assert levels[8192] == 1 and levels[12288] == 1 and levels[10240] == 1
+    assert levels[64] == 1 and levels[96] == 1 and levels[80] == 1
     assert levels[16384] == 2 and levels[65536] == 2 and levels[20480] == 2 and levels[24576] == 2
+    # within a size family the level never drops as m grows
+    for base in (64, 96, 80):
+        fam = sorted(m for m in sizes if m % base == 0 and (m // base) & (m // base - 1) == 0)
+        lv = [levels[m] for m in fam]
+        assert lv == sorted(lv)
     check_all(sizes, f, g, off, h)
 
 
