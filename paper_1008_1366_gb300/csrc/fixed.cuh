@@ -24,11 +24,12 @@
 // Level 2 (m = L1 * L2): the m-point transform as L1-point row transforms
 // and L2-point column transforms (the two-factor split of a DFT):
 //   pass A (column tile): for both residues and both inputs, the L2-point
-//       backward transforms of the columns k1, times zeta_m^{j2 k1},
-//       written row-major to scratch S[j2][k1];
-//   pass B (row group): rows j2 of one residue: L1-point backward
-//       transforms of the f and g rows, product, L1-point forward
-//       transform, times zeta_m^{-j2 k1}, written back over the f row;
+//       backward transforms of the columns k1, written row-major to
+//       scratch S[j2][k1];
+//   pass B (row group): rows j2 of one residue: times zeta_m^{j2 k1},
+//       L1-point backward transforms of the f and g rows, product,
+//       L1-point forward transform, times zeta_m^{-j2 k1}, written back
+//       over the f row;
 //   pass C (column tile): for both residues, the L2-point forward
 //       transforms of the product columns, then the residue
 //       recombination (Eq. (2.2)) into the output.
@@ -62,18 +63,24 @@ __host__ __device__ constexpr int pow2_cap(int E) {
 }
 // radices of an L-point transform with E elements per thread: the largest
 // power of two dividing E (at most 16) repeatedly, the remaining power of
-// two, then the odd factor
+// two, then the odd factor, merged with the power of two that completes E
+// into one compound radix (24 = 8 x 3, 20 = 4 x 5) when L allows it
 __host__ __device__ constexpr Plan make_plan(int L, int E) {
   Plan p{0, {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}};
   const int odd = odd_part(L);
   int rest = L / odd;
+  int last = odd;
+  if (odd > 1 && E % odd == 0 && rest % (E / odd) == 0) {
+    last = E;
+    rest /= E / odd;
+  }
   const int cap = pow2_cap(E);
   while (rest > 1) {
     const int r = rest >= cap ? cap : rest;
     p.r[p.n++] = r;
     rest /= r;
   }
-  if (odd > 1) p.r[p.n++] = odd;
+  if (last > 1) p.r[p.n++] = last;
   return p;
 }
 // elements per thread of the row/level-1 transforms of a size family
@@ -90,6 +97,13 @@ __host__ __device__ constexpr int col_E(int m) {
 }
 __host__ __device__ constexpr int col_width(int m) { return kThreads * col_E(m) / l2_cols(m); }
 __host__ __device__ constexpr int padded(int L) { return (L + (L >> 4) + 2) & ~1; }
+// Element stride between the array pairs (A, B) of consecutive thread groups
+// of T threads.  When several groups share a half-warp (T < 16) the stride
+// is made congruent to T modulo 16, so the groups' contiguous runs fall on
+// disjoint bank pairs instead of the same ones.
+__host__ __device__ constexpr int group_stride(int L, int T) {
+  return T >= 16 ? 2 * padded(L) : 2 * padded(L) + ((T - 2 * padded(L)) % 16 + 16) % 16;
+}
 
 template <int L, int E> struct Fft {
   static constexpr Plan P = make_plan(L, E);
@@ -115,6 +129,90 @@ template <int L, int E, int S, bool FWD> struct Stage {
 };
 
 // ---------------------------------------------------------------------------
+// compound radices R = A B (12 = 4 x 3, 20 = 4 x 5, 24 = 8 x 3) as nested
+// DFTs in registers: with n = B n1 + n2 and k = k1 + A k2,
+//   X[k1 + A k2] = sum_{n2} zeta_B^{n2 k2} zeta_R^{n2 k1} sum_{n1} zeta_A^{n1 k1} x[B n1 + n2]
+// (the Cooley-Tukey split of a DFT; internal twiddles are constants).
+// ---------------------------------------------------------------------------
+template <int R> struct RootConst;
+template <> struct RootConst<12> {
+  static constexpr double c[12] = {1.0, 0.86602540378443871, 0.5, 0.0, -0.5, -0.86602540378443871, -1.0, -0.86602540378443882, -0.5, 0.0, 0.5, 0.86602540378443837};
+  static constexpr double s[12] = {0.0, 0.5, 0.8660254037844386, 1.0, 0.86602540378443871, 0.5, 0.0, -0.5, -0.86602540378443837, -1.0, -0.8660254037844386, -0.5};
+};
+template <> struct RootConst<20> {
+  static constexpr double c[20] = {1.0, 0.95105651629515353, 0.80901699437494745, 0.58778525229247314, 0.30901699437494745, 0.0, -0.30901699437494734, -0.58778525229247303, -0.80901699437494734, -0.95105651629515353, -1.0, -0.95105651629515375, -0.80901699437494756, -0.58778525229247325, -0.30901699437494756, 0.0, 0.30901699437494723, 0.58778525229247292, 0.80901699437494734, 0.95105651629515353};
+  static constexpr double s[20] = {0.0, 0.3090169943749474, 0.58778525229247314, 0.80901699437494745, 0.95105651629515353, 1.0, 0.95105651629515364, 0.80901699437494745, 0.58778525229247325, 0.30901699437494751, 0.0, -0.3090169943749469, -0.58778525229247303, -0.80901699437494734, -0.95105651629515353, -1.0, -0.95105651629515364, -0.80901699437494756, -0.58778525229247336, -0.30901699437494762};
+};
+template <> struct RootConst<24> {
+  static constexpr double c[24] = {1.0, 0.96592582628906831, 0.86602540378443871, 0.70710678118654757, 0.5, 0.25881904510252074, 0.0, -0.25881904510252063, -0.5, -0.70710678118654746, -0.86602540378443871, -0.9659258262890682, -1.0, -0.96592582628906831, -0.86602540378443882, -0.70710678118654791, -0.5, -0.25881904510252063, 0.0, 0.2588190451025203, 0.5, 0.70710678118654735, 0.86602540378443837, 0.96592582628906809};
+  static constexpr double s[24] = {0.0, 0.25881904510252074, 0.5, 0.70710678118654746, 0.8660254037844386, 0.96592582628906831, 1.0, 0.96592582628906831, 0.86602540378443871, 0.70710678118654757, 0.5, 0.25881904510252102, 0.0, -0.25881904510252079, -0.5, -0.70710678118654713, -0.86602540378443837, -0.96592582628906831, -1.0, -0.96592582628906842, -0.8660254037844386, -0.70710678118654768, -0.5, -0.25881904510252157};
+};
+
+// x * zeta_R^{sgn K}, exact for multiples of a quarter turn
+template <int R, int K>
+__device__ __forceinline__ C mul_root(C x, int sgn) {
+  constexpr int k = ((K % R) + R) % R;
+  if constexpr (k == 0) {
+    return x;
+  } else if constexpr (4 * k == R) {
+    return si(x, sgn);
+  } else if constexpr (2 * k == R) {
+    return make_float2(-x.x, -x.y);
+  } else if constexpr (4 * k == 3 * R) {
+    return si(x, -sgn);
+  } else {
+    constexpr float c = (float)RootConst<R>::c[k], s = (float)RootConst<R>::s[k];
+    return mcs(x, c, s, sgn);
+  }
+}
+
+template <int A, int B, int R, int K1, int N2>
+__device__ __forceinline__ void nested_tw(C (&y)[A][B], int sgn) {
+  if constexpr (K1 < A) {
+    if constexpr (N2 < B) {
+      y[K1][N2] = mul_root<R, K1 * N2>(y[K1][N2], sgn);
+      nested_tw<A, B, R, K1, N2 + 1>(y, sgn);
+    } else {
+      nested_tw<A, B, R, K1 + 1, 0>(y, sgn);
+    }
+  }
+}
+
+template <int A, int B>
+__device__ __forceinline__ void rdft_nested(C* x, int sgn) {
+  constexpr int R = A * B;
+  C y[A][B];
+  C t[A];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) t[n1] = x[B * n1 + n2];
+    rdft<A>(t, sgn);
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) y[k1][n2] = t[k1];
+  }
+  nested_tw<A, B, R, 0, 0>(y, sgn);
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    C u[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) u[n2] = y[k1][n2];
+    rdft<B>(u, sgn);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) x[k1 + A * k2] = u[k2];
+  }
+}
+
+// radix-R DFT of the fixed engine: the shared butterflies, or a nested one
+template <int R>
+__device__ __forceinline__ void rdft_fx(C* x, int sgn) {
+  if constexpr (R == 12) rdft_nested<4, 3>(x, sgn);
+  else if constexpr (R == 20) rdft_nested<4, 5>(x, sgn);
+  else if constexpr (R == 24) rdft_nested<8, 3>(x, sgn);
+  else rdft<R>(x, sgn);
+}
+
+// ---------------------------------------------------------------------------
 // shared-memory layouts
 // ---------------------------------------------------------------------------
 struct Contig {   // element x at p[x + x/16]: 16 elements span the 32 banks, one pad word pair
@@ -124,6 +222,29 @@ struct Contig {   // element x at p[x + x/16]: 16 elements span the 32 banks, on
 template <int W> struct Inter {   // column tile: element x of this column at p[x * W]
   C* p;
   __device__ __forceinline__ C& operator[](int x) const { return p[x * W]; }
+};
+
+// ---------------------------------------------------------------------------
+// barriers between stages: the threads that share the arrays, no more.
+// A group of at most 32 threads lies within one warp (__syncwarp); a larger
+// group that is not the whole block uses its own named barrier (id 1 + its
+// index; 0 is the block barrier).
+// ---------------------------------------------------------------------------
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <int T> struct GroupSync {
+  int id;
+  __device__ __forceinline__ void operator()() const {
+    if constexpr (T >= kThreads) {
+      __syncthreads();
+    } else if constexpr (T <= 32) {
+      __syncwarp();
+    } else {
+      static_assert(T % 32 == 0 && kThreads / T < 16, "named barriers cover whole warps");
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(T) : "memory");
+    }
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -152,30 +273,35 @@ __device__ __forceinline__ void scatter(const C* v, int i, const Lay& X) {
   }
 }
 
-// Powers w[q] = w1^q, q < R, of a stage twiddle from exact table values of
-// w1 and (R >= 8) w4 by products of depth at most three:
-// w2 = w1^2, w3 = w2 w1, w8 = w4^2, w_{4a+b} = w_{4a} w_b.  Two table
-// lookups per butterfly instead of R - 1.
-template <int R>
-__device__ __forceinline__ void tw_powers(C* w, C w1, C w4) {
-  w[1] = w1;
-  if constexpr (R > 2) w[2] = cmul(w1, w1);
-  if constexpr (R > 3) w[3] = cmul(w[2], w1);
-  if constexpr (R == 5) w[4] = cmul(w[2], w[2]);
-  if constexpr (R >= 8) {
-    w[4] = w4;
+// Multiplies x[q] (q = 1 .. R-1) by w^q (FWD: conj(w)^q), w = zeta_TN^e,
+// with the powers formed from exact table values at q = 1, 4, 8, 16 (those
+// below R) by products of depth at most four: w2 = w1^2, w3 = w2 w1,
+// w12 = w8 w4, w20 = w16 w4, w_{4a+b} = w_{4a} w_b.  A few table lookups per
+// butterfly instead of R - 1, and each power is applied as soon as it is
+// formed, so only w1, w2, w3 and the current w_{4a} stay live.
+template <int R, bool FWD>
+__device__ __forceinline__ void tw_apply(C* x, const Roots<C>& rt, int e) {
+  auto app = [&](int q, C w) { x[q] = FWD ? cmulc(x[q], w) : cmul(x[q], w); };
+  const C w1 = rt.at(e);
+  app(1, w1);
+  C w2 = w1, w3 = w1;
+  if constexpr (R > 2) { w2 = cmul(w1, w1); app(2, w2); }
+  if constexpr (R > 3) { w3 = cmul(w2, w1); app(3, w3); }
+  if constexpr (R == 5) app(4, cmul(w2, w2));
+  if constexpr (R > 5) {
+    C w4 = w1, w8 = w1, w16 = w1;
 #pragma unroll
-    for (int b = 1; b < 4; ++b) w[4 + b] = cmul(w4, w[b]);
-  }
-  if constexpr (R == 16) {
-    const C w8 = cmul(w4, w4);
-    const C w12 = cmul(w8, w4);
-    w[8] = w8;
-    w[12] = w12;
-#pragma unroll
-    for (int b = 1; b < 4; ++b) {
-      w[8 + b] = cmul(w8, w[b]);
-      w[12 + b] = cmul(w12, w[b]);
+    for (int a = 1; 4 * a < R; ++a) {
+      C wa;
+      if (a == 1) wa = w4 = rt.at(4 * e);
+      else if (a == 2) wa = w8 = rt.at(8 * e);
+      else if (a == 4) wa = w16 = rt.at(16 * e);
+      else if (a == 3) wa = cmul(w8, w4);
+      else wa = cmul(w16, w4);   // a == 5
+      app(4 * a, wa);
+      if (4 * a + 1 < R) app(4 * a + 1, cmul(wa, w1));
+      if (4 * a + 2 < R) app(4 * a + 2, cmul(wa, w2));
+      if (4 * a + 3 < R) app(4 * a + 3, cmul(wa, w3));
     }
   }
 }
@@ -191,14 +317,9 @@ __device__ __forceinline__ void dft(C* v, int i, const Roots<C>& rt) {
     if constexpr (K::Ns > 1) {
       static_assert(TN % (K::Ns * K::R) == 0, "root table must cover the stage");
       const int j = i + b * K::T;
-      const int e = (j % K::Ns) * (TN / (K::Ns * K::R));
-      C w[K::R];
-      tw_powers<K::R>(w, rt.at(e), K::R >= 8 ? rt.at(4 * e) : rt.at(0));
-#pragma unroll
-      for (int q = 1; q < K::R; ++q)
-        v[b * K::R + q] = FWD ? cmulc(v[b * K::R + q], w[q]) : cmul(v[b * K::R + q], w[q]);
+      tw_apply<K::R, FWD>(&v[b * K::R], rt, (j % K::Ns) * (TN / (K::Ns * K::R)));
     }
-    rdft<K::R>(&v[b * K::R], sgn);
+    rdft_fx<K::R>(&v[b * K::R], sgn);
   }
 }
 
@@ -216,46 +337,47 @@ __device__ __forceinline__ int pos(int i, int b, int q) {
 // transform's output at natural index x (e: its register index).  A and B: padded shared arrays of
 // the group.  Every thread of the block calls this (barriers inside).
 // ---------------------------------------------------------------------------
-template <int L, int E, int TN, int S>
+template <int L, int E, int TN, int S, class Sy>
 __device__ __forceinline__ void bwd_middle(C* v, int i, bool act, const Contig& A, const Contig& B,
-                                           const Roots<C>& rt) {
+                                           const Roots<C>& rt, const Sy& sync) {
   constexpr int n = Fft<L, E>::n;
   if constexpr (S < n - 1) {
     if (act) {
       gather<L, E, S, false>(v, i, A);
       dft<L, E, S, false, TN>(v, i, rt);
     }
-    __syncthreads();
+    sync();
     if (act) {
       scatter<L, E, S, false>(v, i, A);
       gather<L, E, S, false>(v, i, B);
       dft<L, E, S, false, TN>(v, i, rt);
     }
-    __syncthreads();
+    sync();
     if (act) scatter<L, E, S, false>(v, i, B);
-    bwd_middle<L, E, TN, S + 1>(v, i, act, A, B, rt);
+    bwd_middle<L, E, TN, S + 1>(v, i, act, A, B, rt, sync);
   }
 }
 
 // middle stages of one array in place (gather, barrier, scatter, barrier)
-template <int L, int E, int TN, bool FWD, int S, class Lay>
-__device__ __forceinline__ void one_middle(C* v, int i, bool act, const Lay& A, const Roots<C>& rt) {
+template <int L, int E, int TN, bool FWD, int S, class Lay, class Sy>
+__device__ __forceinline__ void one_middle(C* v, int i, bool act, const Lay& A, const Roots<C>& rt,
+                                           const Sy& sync) {
   constexpr int n = Fft<L, E>::n;
   if constexpr (S < n - 1) {
     if (act) {
       gather<L, E, S, FWD>(v, i, A);
       dft<L, E, S, FWD, TN>(v, i, rt);
     }
-    __syncthreads();
+    sync();
     if (act) scatter<L, E, S, FWD>(v, i, A);
-    __syncthreads();
-    one_middle<L, E, TN, FWD, S + 1>(v, i, act, A, rt);
+    sync();
+    one_middle<L, E, TN, FWD, S + 1>(v, i, act, A, rt, sync);
   }
 }
 
-template <int L, int E, int TN, class Ld, class St>
+template <int L, int E, int TN, class Ld, class St, class Sy>
 __device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, const Roots<C>& rt,
-                                             const Ld& ld, const St& st) {
+                                             const Ld& ld, const St& st, const Sy& sync) {
   using F = Fft<L, E>;
   constexpr int n = F::n;
   static_assert(n >= 2, "at least two stages");
@@ -274,15 +396,15 @@ __device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, cons
       scatter<L, E, 0, false>(v, i, arr ? B : A);
     }
   }
-  __syncthreads();
-  bwd_middle<L, E, TN, 1>(v, i, act, A, B, rt);
+  sync();
+  bwd_middle<L, E, TN, 1>(v, i, act, A, B, rt, sync);
   // last backward stage: thread-private positions (k = j), in place
   if (act) {
     gather<L, E, n - 1, false>(v, i, A);
     dft<L, E, n - 1, false, TN>(v, i, rt);
     scatter<L, E, n - 1, false>(v, i, A);
   }
-  if constexpr (n > 2) __syncthreads();
+  if constexpr (n > 2) sync();
   if (act) {
     gather<L, E, n - 1, false>(v, i, B);
     dft<L, E, n - 1, false, TN>(v, i, rt);
@@ -296,10 +418,10 @@ __device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, cons
     // first forward stage: same radix and positions, no twiddles
     dft<L, E, 0, true, TN>(v, i, rt);
   }
-  __syncthreads();
+  sync();
   if (act) scatter<L, E, 0, true>(v, i, A);
-  __syncthreads();
-  one_middle<L, E, TN, true, 1>(v, i, act, A, rt);
+  sync();
+  one_middle<L, E, TN, true, 1>(v, i, act, A, rt, sync);
   // last forward stage: thread-private positions
   if (act) {
     gather<L, E, n - 1, true>(v, i, A);
@@ -325,7 +447,7 @@ __device__ __forceinline__ void column(C* v, int i, C* Dp, const Roots<C>& rt, c
   dft<L, E, 0, FWD, TN>(v, i, rt);
   scatter<L, E, 0, FWD>(v, i, D);
   __syncthreads();
-  one_middle<L, E, TN, FWD, 1>(v, i, true, D, rt);
+  one_middle<L, E, TN, FWD, 1>(v, i, true, D, rt, BlockSync{});
   gather<L, E, n - 1, FWD>(v, i, D);
   dft<L, E, n - 1, FWD, TN>(v, i, rt);
   using K = Stage<L, E, n - 1, FWD>;

@@ -67,8 +67,12 @@ template <int M> struct Shape {
   static constexpr int EC = l1 ? 16 : col_E(M);
   static_assert(l1 || (L1 % W == 0 && (2 * L2) % GR == 0 && L1 * L2 == M), "level-2 tiling must be exact");
   static_assert(!l1 || kThreads % T == 0, "level-1 groups must tile the block");
-  static constexpr int smem = l1 ? G * 2 * padded(M) * 8
-                                 : (GR * 2 * padded(L1) * 8 > W * L2 * 8 ? GR * 2 * padded(L1) * 8 : W * L2 * 8);
+  static constexpr int smem = l1 ? G * group_stride(M, T) * 8
+                                 : (GR * group_stride(L1, T1) * 8 > W * L2 * 8 ? GR * group_stride(L1, T1) * 8
+                                                                                 : W * L2 * 8);
+  // two blocks per SM: 228 KB per SM less 1 KB reserved per block and the
+  // static shared variables
+  static_assert(smem + kRootsMax * 8 <= (233472 - 2 * 1024) / 2 - 64, "two blocks fit on an SM");
 };
 
 // ---------------------------------------------------------------------------
@@ -81,16 +85,17 @@ template <int M> struct Shape {
 template <int M, int R>
 __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C* sm, Roots<C> rt) {
   using S = Shape<M>;
-  constexpr int E = S::E, T = S::T, PL = padded(M), TN = 2 * M;
+  constexpr int E = S::E, T = S::T, PL = padded(M), GS = group_stride(M, T), TN = 2 * M;
   const int gi = threadIdx.x / T, i = threadIdx.x % T;
   const bool act = gi < count;
   const int64_t off = act ? a->off[a->order[first + gi]] : 0;
   const C* f = a->f + off;
   const C* g = a->g + off;
   C* h = a->h + off;
-  C* A = sm + gi * 2 * PL;
+  C* A = sm + gi * GS;
   C* B = A + PL;
   const float sc = 1.0f / (float)(2 * M);
+  const GroupSync<T> sync{1 + gi};
   // groups past `count` transform zeros and store nothing: the stages
   // themselves carry no condition
   const C zero = make_float2(0.f, 0.f);
@@ -100,26 +105,42 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
         i, true, A, B, rt, [&](int x, int arr, int) { return act ? __ldg((arr ? g : f) + x) : zero; },
         [&](int x, int, C v) {
           if (act) h[x] = cscale(v, sc);
-        });
-  } else {
-    // residue 1: inputs times zeta_{2m}^k (looked up once for f and g),
-    // output times zeta_{2m}^{-k} (Eq. (2.2))
-    C tw[E];
-    conv_residue<M, E, TN>(
-        i, true, A, B, rt,
-        [&](int x, int arr, int e) {
-          if (arr == 0) tw[e] = rt.at(x);
-          return act ? cmul(__ldg((arr ? g : f) + x), tw[e]) : zero;
         },
-        [&](int x, int, C v) {
-          if (act) h[x] = cadd(h[x], cscale(cmulc(v, rt.at(x)), sc));
-        });
+        sync);
+  } else {
+    // residue 1: inputs times zeta_{2m}^k, output times zeta_{2m}^{-k}
+    // (Eq. (2.2)).  The last forward stage leaves register e at the position
+    // the first backward stage loaded into it, so one lookup per element
+    // serves f, g and the output.
+    C tw[E];
+    auto ld = [&](int x, int arr, int e) {
+      if (arr == 0) tw[e] = rt.at(x);
+      return act ? cmul(__ldg((arr ? g : f) + x), tw[e]) : zero;
+    };
+    if constexpr (E <= 20) {
+      conv_residue<M, E, TN>(
+          i, true, A, B, rt, ld,
+          [&](int x, int e, C v) {
+            if (act) h[x] = cadd(h[x], cscale(cmulc(v, tw[e]), sc));
+          },
+          sync);
+    } else {
+      // E = 24: a second lookup is cheaper than 24 registers held through
+      // the whole residue
+      conv_residue<M, E, TN>(
+          i, true, A, B, rt, ld,
+          [&](int x, int, C v) {
+            if (act) h[x] = cadd(h[x], cscale(cmulc(v, rt.at(x)), sc));
+          },
+          sync);
+    }
   }
 }
 
-// pass A: column tile `tile` of level-2 instance l
+// pass A: column tile `tile` of level-2 instance l.  Each pass is its own
+// function so that registers are allocated per pass.
 template <int M>
-__device__ __forceinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, const Roots<C>& rt) {
+__device__ __noinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
   using S = Shape<M>;
   constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 2 * M;
   using K = Stage<L2, E, 0, false>;
@@ -127,33 +148,28 @@ __device__ __forceinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, c
   const int k1 = tile * W + c;
   const L2Inst in = a->l2[l];
   C* scr = a->scratch + in.scr;
-  // both inputs' columns are loaded before any transform (their latency
-  // overlaps the first transforms)
-  C raw[2][E];
+  // residue-1 input twiddles zeta_{2m}^{k1 + L1 k2}, shared by f and g
+  C tw[E];
 #pragma unroll
+  for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+    for (int q = 0; q < K::R; ++q) tw[b * K::R + q] = rt.at(k1 + L1 * pos<L2, E, 0, false>(i, b, q));
+#pragma unroll 1
   for (int arr = 0; arr < 2; ++arr) {
     const C* x = (arr ? a->g : a->f) + in.off + k1;
+    C raw[E];
 #pragma unroll
     for (int b = 0; b < K::NB; ++b)
 #pragma unroll
-      for (int q = 0; q < K::R; ++q) raw[arr][b * K::R + q] = __ldg(x + L1 * pos<L2, E, 0, false>(i, b, q));
-  }
-#pragma unroll
-  for (int arr = 0; arr < 2; ++arr) {
+      for (int q = 0; q < K::R; ++q) raw[b * K::R + q] = __ldg(x + L1 * pos<L2, E, 0, false>(i, b, q));
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
       C v[E];
 #pragma unroll
-      for (int b = 0; b < K::NB; ++b)
-#pragma unroll
-        for (int q = 0; q < K::R; ++q) {
-          const int e = b * K::R + q;
-          v[e] = r ? cmul(raw[arr][e], rt.at(k1 + L1 * pos<L2, E, 0, false>(i, b, q))) : raw[arr][e];
-        }
+      for (int e = 0; e < E; ++e) v[e] = r ? cmul(raw[e], tw[e]) : raw[e];
+      // S[j2][k1]; the factor zeta_m^{j2 k1} is applied in pass B
       C* dst = scr + (size_t)(2 * r + arr) * M + k1;
-      column<L2, E, W, TN, false>(v, i, sm + c, rt, [&](int j2, int, C y) {
-        __stcg(dst + (size_t)j2 * L1, cmul(y, rt.at(2 * j2 * k1)));
-      });
+      column<L2, E, W, TN, false>(v, i, sm + c, rt, [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
       __syncthreads();
     }
   }
@@ -161,25 +177,42 @@ __device__ __forceinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, c
 
 // pass B: row group `unit` (rows (r, j2), r = row / L2) of level-2 instance l
 template <int M>
-__device__ __forceinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, const Roots<C>& rt) {
+__device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Roots<C> rt) {
   using S = Shape<M>;
-  constexpr int L1 = S::L1, L2 = S::L2, E1 = S::E1, T1 = S::T1, GR = S::GR, PL = padded(L1), TN = 2 * M;
+  constexpr int L1 = S::L1, L2 = S::L2, E1 = S::E1, T1 = S::T1, GR = S::GR, PL = padded(L1),
+                GS = group_stride(L1, T1), TN = 2 * M;
   const int gi = threadIdx.x / T1, i = threadIdx.x % T1;
   const int row = unit * GR + gi;
   const int r = row / L2, j2 = row % L2;
   C* scr = a->scratch + a->l2[l].scr;
   C* sf = scr + (size_t)(2 * r) * M + (size_t)j2 * L1;
   const C* sg = scr + (size_t)(2 * r + 1) * M + (size_t)j2 * L1;
-  C* A = sm + gi * 2 * PL;
+  C* A = sm + gi * GS;
   C* B = A + PL;
-  conv_residue<L1, E1, TN>(
-      i, true, A, B, rt, [&](int x, int arr, int) { return __ldcg((arr ? sg : (const C*)sf) + x); },
-      [&](int x, int, C v) { __stcg(sf + x, cmulc(v, rt.at(2 * j2 * x))); });
+  // inputs times zeta_m^{j2 k1} (one lookup for f, g and the output, whose
+  // register e sits at the same position), output times zeta_m^{-j2 k1}
+  const GroupSync<T1> sync{1 + gi};
+  if constexpr (E1 <= 20) {
+    C tw[E1];
+    conv_residue<L1, E1, TN>(
+        i, true, A, B, rt,
+        [&](int x, int arr, int e) {
+          if (arr == 0) tw[e] = rt.at(2 * j2 * x);
+          return cmul(__ldcg((arr ? sg : (const C*)sf) + x), tw[e]);
+        },
+        [&](int x, int e, C v) { __stcg(sf + x, cmulc(v, tw[e])); }, sync);
+  } else {
+    // E1 = 24: one lookup per use is cheaper than 24 more live registers
+    conv_residue<L1, E1, TN>(
+        i, true, A, B, rt,
+        [&](int x, int arr, int) { return cmul(__ldcg((arr ? sg : (const C*)sf) + x), rt.at(2 * j2 * x)); },
+        [&](int x, int, C v) { __stcg(sf + x, cmulc(v, rt.at(2 * j2 * x))); }, sync);
+  }
 }
 
 // pass C: column tile `tile` of level-2 instance l, both residues, output
 template <int M>
-__device__ __forceinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, const Roots<C>& rt) {
+__device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
   using S = Shape<M>;
   constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 2 * M;
   using K = Stage<L2, E, 0, true>;
