@@ -206,6 +206,20 @@ dc_status dc_batched_plan_launches(const dc_batched_plan* plan, int32_t* launche
 dc_status dc_batched_plan_describe(const dc_batched_plan* plan, int32_t i, int64_t* m,
                                    int32_t* level, int32_t* nt, int32_t* l1, int32_t* l2,
                                    int32_t* w);
+/* Queue order of an FP32 plan on the fixed-shape engine (every size in the
+ * set {2^a, 3*2^a, 5*2^a}, 64 <= m <= 65536): *batch_target = column tiles
+ * per batch of two-level instances (the pipeline distance between their
+ * passes), *l1_mode = placement of the one-level work (0 after the
+ * two-level pipeline, 1 the larger half spread over it, 2 before it).  No
+ * counterpart in the paper (a GPU scheduling choice).  DC_ERR_ARG for other
+ * plans. */
+dc_status dc_batched_plan_schedule(const dc_batched_plan* plan, int32_t* batch_target,
+                                   int32_t* l1_mode);
+/* Rebuilds the queue of such a plan with the given order (batch_target >= 1,
+ * 0 <= l1_mode <= 2); the result does not depend on it, only the time does.
+ * The workspace size may change: query it again.  Not while a launch of the
+ * plan is in flight.  DC_ERR_ARG for other plans or values. */
+dc_status dc_batched_plan_set_schedule(dc_batched_plan* plan, int32_t batch_target, int32_t l1_mode);
 dc_status dc_conv_complex_1d_batched(const dc_batched_plan* plan, const void* f, const void* g,
                                      void* h, void* work, size_t work_bytes, void* stream);
 dc_status dc_batched_plan_destroy(dc_batched_plan* plan);

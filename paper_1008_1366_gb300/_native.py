@@ -40,6 +40,8 @@ SIGNATURES = {
     "dc_batched_plan_workspace_size": [_vp, ctypes.POINTER(_sz)],
     "dc_batched_plan_launches": [_vp, ctypes.POINTER(_i32)],
     "dc_batched_plan_describe": [_vp, _i32, ctypes.POINTER(_i64)] + [ctypes.POINTER(_i32)] * 5,
+    "dc_batched_plan_schedule": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
+    "dc_batched_plan_set_schedule": [_vp, _i32, _i32],
     "dc_conv_complex_1d_batched": [_vp, _vp, _vp, _vp, _vp, _sz, _vp],
     "dc_batched_plan_destroy": [_vp],
 }

@@ -206,8 +206,25 @@ class BatchedPlan:
             i += 1
         return out
 
+    def schedule(self):
+        """(batch_target, l1_mode) of the fixed-shape engine's task queue, or
+        None for plans on the runtime-shaped engine."""
+        t, mo = ctypes.c_int32(0), ctypes.c_int32(0)
+        if _native.lib().dc_batched_plan_schedule(self.handle, ctypes.byref(t), ctypes.byref(mo)) != 0:
+            return None
+        return t.value, mo.value
+
+    def set_schedule(self, batch_target, l1_mode):
+        """Rebuilds the task queue in the given order (dc_batched_plan_set_schedule)."""
+        check(_native.lib().dc_batched_plan_set_schedule(self.handle, int(batch_target), int(l1_mode)),
+              "dc_batched_plan_set_schedule")
+        ws = ctypes.c_size_t(0)
+        check(_native.lib().dc_batched_plan_workspace_size(self.handle, ctypes.byref(ws)), "workspace")
+        self.workspace_bytes = int(ws.value)
+        self._work = None
+
     def workspace(self, device):
-        if self._work is None or self._work.device != device:
+        if self._work is None or self._work.device != device or self._work.numel() < self.workspace_bytes:
             self._work = _work(self.workspace_bytes, device)
         return self._work
 

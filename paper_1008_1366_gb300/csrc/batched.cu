@@ -47,7 +47,7 @@ struct dc_batched_plan {
   fx::L2Inst* d_l2 = nullptr;
   const float2* tabs[fx::kNumSizes] = {};
   size_t cnt_bytes = 0;   // header + counters, zeroed before each launch
-  int fx_target = 0;      // column tiles per level-2 batch
+  fx::Schedule fx_sched{0, 0};   // queue order of the fixed engine
   std::vector<int64_t> off_host;
 };
 
@@ -230,8 +230,8 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
   dc_status st = fx::prepare_kernel(smem_all, &bps);
   if (st != DC_OK) return st;
   p->grid = bps * device_info().sms;
-  int target = p->grid / 2;
-  if (!fx::build_plan(m, n, off.data(), target, &p->hp)) return DC_ERR_SIZE;
+  const fx::Schedule dflt{p->grid / 2, 0};
+  if (!fx::build_plan(m, n, off.data(), dflt, &p->hp)) return DC_ERR_SIZE;
   p->smem = p->hp.smem;
   for (int c : p->hp.codes) {
     const void* tw = nullptr;
@@ -241,27 +241,29 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
   }
   st = fx_upload(p, off);
   if (st != DC_OK) return st;
+  p->fx_sched = dflt;
   if (flags & DC_PLAN_AUTOTUNE) {
-    // the pipeline distance between the level-2 passes: trades waiting
-    // against the scratch footprint in L2
+    // the queue order: pipeline distance between the level-2 passes (waits
+    // against scratch footprint in L2) and the placement of level-1 work
     cudaStream_t s;
     DC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    int best = target;
+    fx::Schedule best = dflt;
     float tbest = fx_time(p, off, s);
-    for (int cand : {p->grid / 4, p->grid, 2 * p->grid}) {
-      if (cand < 1 || !fx::build_plan(m, n, off.data(), cand, &p->hp)) continue;
-      if (fx_upload(p, off) != DC_OK) continue;
-      const float t = fx_time(p, off, s);
-      if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; best = cand; }
+    for (int cand : {p->grid / 4, p->grid / 2, p->grid}) {
+      for (int mode = 0; mode < fx::kL1Modes; ++mode) {
+        const fx::Schedule sc{cand, mode};
+        if (cand < 1 || (cand == dflt.batch_target && mode == dflt.l1_mode)) continue;
+        if (!fx::build_plan(m, n, off.data(), sc, &p->hp) || fx_upload(p, off) != DC_OK) continue;
+        const float t = fx_time(p, off, s);
+        if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; best = sc; }
+      }
     }
     cudaStreamDestroy(s);
     cudaGetLastError();
     if (!fx::build_plan(m, n, off.data(), best, &p->hp)) return DC_ERR_SIZE;
     st = fx_upload(p, off);
     if (st != DC_OK) return st;
-    p->fx_target = best;
-  } else {
-    p->fx_target = target;
+    p->fx_sched = best;
   }
   return DC_OK;
 }
@@ -373,6 +375,25 @@ dc_status dc_batched_plan_workspace_size(const dc_batched_plan* p, size_t* bytes
 dc_status dc_batched_plan_launches(const dc_batched_plan* p, int32_t* launches) {
   if (!p || !launches) return DC_ERR_ARG;
   *launches = (!p->fx && (p->flags & DC_PLAN_ONE_PER_LAUNCH)) ? (int32_t)p->items.size() : 1;
+  return DC_OK;
+}
+
+dc_status dc_batched_plan_schedule(const dc_batched_plan* p, int32_t* batch_target, int32_t* l1_mode) {
+  if (!p || !p->fx) return DC_ERR_ARG;
+  if (batch_target) *batch_target = p->fx_sched.batch_target;
+  if (l1_mode) *l1_mode = p->fx_sched.l1_mode;
+  return DC_OK;
+}
+
+dc_status dc_batched_plan_set_schedule(dc_batched_plan* p, int32_t batch_target, int32_t l1_mode) {
+  if (!p || !p->fx || batch_target < 1 || l1_mode < 0 || l1_mode >= fx::kL1Modes) return DC_ERR_ARG;
+  std::vector<int64_t> ms(p->n);
+  for (int32_t i = 0; i < p->n; ++i) ms[i] = p->off_host[i + 1] - p->off_host[i];
+  const fx::Schedule sc{batch_target, l1_mode};
+  if (!fx::build_plan(ms.data(), p->n, p->off_host.data(), sc, &p->hp)) return DC_ERR_SIZE;
+  dc_status st = fx_upload(p, p->off_host);
+  if (st != DC_OK) return st;
+  p->fx_sched = sc;
   return DC_OK;
 }
 

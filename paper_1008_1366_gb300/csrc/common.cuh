@@ -40,7 +40,9 @@ struct WorkHeader {
   int32_t status;     // DC_OK or the first error code a kernel recorded
   int32_t detail;     // kernel-specific detail of that error
   uint32_t counter;   // persistent-queue counter, reset before each launch
-  uint32_t pad[61];
+  uint32_t waited;    // task-queue kernels: tasks that found a dependency unmet
+  unsigned long long wait_cycles;   // and the SM cycles they spent waiting
+  uint32_t pad[58];
 };
 static_assert(sizeof(WorkHeader) == 256, "workspace header is 256 bytes");
 

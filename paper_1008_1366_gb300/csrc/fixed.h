@@ -70,10 +70,20 @@ struct HostPlan {
   std::vector<int> codes;   // distinct size codes of the plan
 };
 
+// Order of the task queue.  batch_target: column tiles per batch of level-2
+// instances (the pipeline distance between passes).  l1_mode: where the
+// level-1 tasks go (largest first in every mode): 0 after the level-2
+// pipeline, 1 the larger half spread over the pipeline and the rest after
+// it, 2 before it.
+struct Schedule {
+  int batch_target;
+  int l1_mode;
+};
+constexpr int kL1Modes = 3;
+
 // Builds the task queue for n instances of sizes m[i] at element offsets
-// off[i] (all sizes must have a code).  batch_target: column tiles per
-// batch of level-2 instances (the pipeline distance between passes).
-bool build_plan(const int64_t* m, int32_t n, const int64_t* off, int batch_target, HostPlan* out);
+// off[i] (all sizes must have a code).
+bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc, HostPlan* out);
 
 // kernel attributes, occupancy
 dc_status prepare_kernel(int smem, int* blocks_per_sm);

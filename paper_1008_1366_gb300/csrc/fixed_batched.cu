@@ -59,7 +59,9 @@ template <int M> struct Shape {
   static constexpr int L2 = l1 ? 128 : l2_cols(M);
   static constexpr int L1 = l1 ? 128 : M / L2;
   static constexpr int W = col_width(l1 ? 16384 : M);
-  static constexpr int E1 = family_E(L1);
+  // rows: E = 12 for the 3 * 2^a family (24 elements per thread spill in
+  // the row pass), else the family's E
+  static constexpr int E1 = odd_part(L1) == 3 ? 12 : family_E(L1);
   static constexpr int T1 = L1 / E1;
   static constexpr int GR = kThreads / T1;
   static constexpr int nA = L1 / W;
@@ -253,14 +255,22 @@ __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C
   }
 }
 
-// bounded wait until *c >= need (thread 0 only); false on timeout
-__device__ __forceinline__ bool wait_geq(const uint32_t* c, uint32_t need) {
+// bounded wait until *c >= need (thread 0 only); false on timeout.  A wait
+// that was not satisfied at once adds its cycles to the header's counters.
+__device__ __forceinline__ bool wait_geq(const uint32_t* c, uint32_t need, WorkHeader* hdr) {
   const long long t0 = clock64();
-  for (;;) {
+  for (int it = 0;; ++it) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
-    if (v >= need) return true;
-    if (clock64() - t0 > (1ll << 32)) return false;   // about two seconds
+    const long long dt = clock64() - t0;
+    if (v >= need) {
+      if (it > 0) {
+        atomicAdd(&hdr->waited, 1u);
+        atomicAdd(&hdr->wait_cycles, (unsigned long long)dt);
+      }
+      return true;
+    }
+    if (dt > (1ll << 32)) return false;   // about two seconds
     __nanosleep(256);
   }
 }
@@ -286,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 2) fx_kernel(const __grid_constant__
       if (idx < (uint32_t)a.ntasks) {
         t = a.tasks[idx];
         next = atomicAdd(&a.hdr->counter, 1u);
-        if (t.widx >= 0 && !wait_geq(a.cnt + t.widx, t.wneed)) {
+        if (t.widx >= 0 && !wait_geq(a.cnt + t.widx, t.wneed, a.hdr)) {
           ok = 0;
           record_error(a.hdr, DC_ERR_TIMEOUT, (int)idx);
         }
@@ -372,7 +382,8 @@ void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W) {
   *W = t.lvl[code] == 1 ? 0 : t.w[code];
 }
 
-bool build_plan(const int64_t* m, int32_t n, const int64_t* off, int batch_target, HostPlan* out) {
+bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc, HostPlan* out) {
+  const int batch_target = std::max(1, sc.batch_target);
   const Tables& tb = tables();
   HostPlan& P = *out;
   P = HostPlan{};
@@ -472,17 +483,22 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, int batch_targe
       }
     }
   };
+  size_t li = 0;
+  auto take_l1 = [&](size_t k) {
+    for (size_t e = 0; e < k && li < l1tasks.size(); ++e) P.tasks.push_back(l1tasks[li++]);
+  };
+  if (sc.l1_mode == 2) take_l1(l1tasks.size());
+  // mode 1: the larger half of the level-1 tasks, spread evenly over the
+  // pipeline, fills the waits between dependent passes
+  const size_t spread = sc.l1_mode == 1 ? l1tasks.size() / 2 : 0;
   for (int s = 0; s < nbat; ++s) {
     emit(T_A, s);
     if (s >= 1) emit(T_B, s - 1);
     if (s >= 2) emit(T_C, s - 2);
+    if (spread) take_l1(spread * (size_t)(s + 1) / (size_t)nbat - li);
   }
   // drain the pipeline with level-1 work between the last passes
-  size_t li = 0;
-  const size_t chunk = std::max<size_t>(1, (size_t)std::max(1, batch_target) * 2);
-  auto take_l1 = [&](size_t k) {
-    for (size_t e = 0; e < k && li < l1tasks.size(); ++e) P.tasks.push_back(l1tasks[li++]);
-  };
+  const size_t chunk = (size_t)batch_target * 2;
   if (nbat >= 1) {
     take_l1(chunk);
     emit(T_B, nbat - 1);

@@ -122,3 +122,26 @@ def test_special_inputs(dc):
     for i, m in enumerate(sizes):
         a, b = off[i], off[i + 1]
         assert rel_l2(h[a:b], g[a:b]) <= fp32_tol(2 * m)
+
+
+def test_schedules_give_identical_results(dc):
+    # the queue order changes timing only: every schedule gives the same bits
+    sizes = [65536] * 3 + [24576] * 4 + [640] * 30 + [64] * 70 + [12288] * 2
+    f, g, off = synthetic.batched_inputs(sizes, 26)
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex64)
+    assert plan.schedule() is not None
+    tf = torch.tensor(f, dtype=torch.complex64, device="cuda")
+    tg = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    ref = plan(tf, tg).clone()
+    for target in (1, 7, 152):
+        for mode in (0, 1, 2):
+            plan.set_schedule(target, mode)
+            assert plan.schedule() == (target, mode)
+            work = plan.workspace(tf.device)
+            h = plan(tf, tg, work=work)
+            torch.cuda.synchronize()
+            assert dc.read_status(work) == (0, 0)
+            assert torch.equal(h, ref), (target, mode)
+    check_all(sizes, f, g, off, ref.cpu().numpy())
+    fp64 = dc.BatchedPlan(sizes, dtype=torch.complex128)
+    assert fp64.schedule() is None
