@@ -40,7 +40,7 @@ METRIC = "dealiased convs/s (FP32 batched, one persistent launch)"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
@@ -105,6 +105,8 @@ class Clocks:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        if self.proc:
+            time.sleep(1.0)   # nvidia-smi's first sample lands about a second after start
         return self
 
     def __exit__(self, *exc):
@@ -329,7 +331,7 @@ def main():
     tf = torch.tensor(f, dtype=torch.complex64, device=dev)
     tg = torch.tensor(g, dtype=torch.complex64, device=dev)
     th = torch.empty_like(tf)
-    plan = dcl.BatchedPlan(ms, dtype=torch.complex64)
+    plan = dcl.BatchedPlan(ms, dtype=torch.complex64, flags=dcl.api.PLAN_AUTOTUNE)
     work = plan.workspace(dev)
     stream = torch.cuda.Stream(device=dev)
 
@@ -455,7 +457,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if n_inst == N_INST else WORKLOAD.replace("4096", str(n_inst)), "instances_per_gpu": n_inst, "total_elements_per_gpu": total,
                        "seed": SEED, "l2": "inputs larger than L2 (%.2f GB per step)" % (alg_bytes / 1e9),
-                       "parallelism": f"{world} independent batches"},
+                       "parallelism": f"{world} independent batches",
+                       "schedule": plan.schedule()},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "convs/s", "h2d_bytes_per_step": 2 * total * 8,

@@ -222,6 +222,14 @@ dc_status dc_batched_plan_schedule(const dc_batched_plan* plan, int32_t* batch_t
 dc_status dc_batched_plan_set_schedule(dc_batched_plan* plan, int32_t batch_target, int32_t l1_mode);
 dc_status dc_conv_complex_1d_batched(const dc_batched_plan* plan, const void* f, const void* g,
                                      void* h, void* work, size_t work_bytes, void* stream);
+/* Failure-path self-test, no counterpart in the paper: launches the
+ * fixed-shape batched kernel on a one-task queue whose dependency counter
+ * nothing advances, with a wait limit of `cycles` SM cycles.  The task's
+ * bounded wait runs out and the kernel records DC_ERR_TIMEOUT (detail: the
+ * task index, 0) in the status word of `work` (>= 1024 bytes, 256-aligned,
+ * device memory), readable with dc_read_status after the stream completes.
+ * Nothing faults or hangs.  DC_ERR_ARG / ALIGN / NOMEM on bad arguments. */
+dc_status dc_selftest_wait_timeout(void* work, size_t work_bytes, int64_t cycles, void* stream);
 dc_status dc_batched_plan_destroy(dc_batched_plan* plan);
 
 #ifdef __cplusplus

@@ -42,6 +42,7 @@ SIGNATURES = {
     "dc_batched_plan_describe": [_vp, _i32, ctypes.POINTER(_i64)] + [ctypes.POINTER(_i32)] * 5,
     "dc_batched_plan_schedule": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "dc_batched_plan_set_schedule": [_vp, _i32, _i32],
+    "dc_selftest_wait_timeout": [_vp, _sz, _i64, _vp],
     "dc_conv_complex_1d_batched": [_vp, _vp, _vp, _vp, _vp, _sz, _vp],
     "dc_batched_plan_destroy": [_vp],
 }

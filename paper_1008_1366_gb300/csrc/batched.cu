@@ -184,6 +184,7 @@ dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void
   a.hdr = (WorkHeader*)work;
   a.cnt = (uint32_t*)((char*)work + sizeof(WorkHeader));
   a.scratch = (float2*)((char*)work + p->cnt_bytes);
+  a.wait_limit = fx::kWaitLimit;
   for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
   return fx::launch(a, p->grid, p->smem, s);
 }
@@ -376,6 +377,32 @@ dc_status dc_batched_plan_launches(const dc_batched_plan* p, int32_t* launches) 
   if (!p || !launches) return DC_ERR_ARG;
   *launches = (!p->fx && (p->flags & DC_PLAN_ONE_PER_LAUNCH)) ? (int32_t)p->items.size() : 1;
   return DC_OK;
+}
+
+dc_status dc_selftest_wait_timeout(void* work, size_t work_bytes, int64_t cycles, void* stream) {
+  // header | one counter (never advanced) | one task waiting for it
+  const size_t need = 256 + 256 + sizeof(fx::Task);
+  if (!work || cycles < 1) return DC_ERR_ARG;
+  if ((uintptr_t)work % 256) return DC_ERR_ALIGN;
+  if (work_bytes < need) return DC_ERR_NOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  int bps = 0;
+  int smem = 0;
+  for (int c = 0; c < fx::kNumSizes; ++c) smem = std::max(smem, fx::code_smem(c));
+  dc_status st = fx::prepare_kernel(smem, &bps);
+  if (st != DC_OK) return st;
+  static const fx::Task task{(fx::T_B << 8) | 0, 0, 0, 0, 1u, -1};
+  char* w = (char*)work;
+  DC_CUDA_TRY(cudaMemsetAsync(w, 0, 512, s));
+  DC_CUDA_TRY(cudaMemcpyAsync(w + 512, &task, sizeof(task), cudaMemcpyHostToDevice, s));
+  fx::FxArgs a{};
+  a.tasks = (const fx::Task*)(w + 512);
+  a.ntasks = 1;
+  a.hdr = (WorkHeader*)w;
+  a.cnt = (uint32_t*)(w + 256);
+  a.wait_limit = cycles;
+  // one block: it takes the task, waits, records the timeout and leaves
+  return fx::launch(a, 1, fx::code_smem(0), s);
 }
 
 dc_status dc_batched_plan_schedule(const dc_batched_plan* p, int32_t* batch_target, int32_t* l1_mode) {

@@ -48,8 +48,11 @@ struct FxArgs {
   uint32_t* cnt;           // dependency counters, zero before each launch
   WorkHeader* hdr;         // status word and queue counter, zero before each launch
   float2* scratch;
+  long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
   const float2* tab[kNumSizes];   // root tables zeta_{2m}^i, i < 2m, per size code
 };
+
+constexpr long long kWaitLimit = 1ll << 32;   // about two seconds at 2 GHz
 
 // size code of m, or -1 when m is not in the set
 int size_code(int64_t m);

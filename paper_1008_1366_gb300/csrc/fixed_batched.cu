@@ -30,6 +30,14 @@
 namespace dc {
 namespace fx {
 
+// Drops a 128-byte line of dead scratch from L2 without writing it back to
+// HBM (the data were read for the last time; the next user overwrites
+// them).  Without it L2 evicts the dead lines to DRAM, more than doubling
+// the kernel's write traffic.
+__device__ __forceinline__ void discard_l2(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 // size codes: 2^6..2^16, 3*2^5..3*2^14, 5*2^4..5*2^13
 __host__ __device__ constexpr int size_of_code(int c) {
   return c < 11 ? (64 << c) : (c < 21 ? (96 << (c - 11)) : (80 << (c - 21)));
@@ -210,6 +218,9 @@ __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Root
         [&](int x, int arr, int) { return cmul(__ldcg((arr ? sg : (const C*)sf) + x), rt.at(2 * j2 * x)); },
         [&](int x, int, C v) { __stcg(sf + x, cmulc(v, rt.at(2 * j2 * x))); }, sync);
   }
+  // the g row was read for the last time (every thread of the group loaded
+  // its part before the group's first barrier)
+  for (int ln = i; ln < L1 / 16; ln += T1) discard_l2(sg + ln * 16);
 }
 
 // pass C: column tile `tile` of level-2 instance l, both residues, output
@@ -240,6 +251,13 @@ __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Root
     const int k = k1 + L1 * k2;
     h[(size_t)L1 * k2] = cscale(cadd(y0[e], cmulc(y, rt.at(k))), sc);
   });
+  // both residues' product columns of the tile were read for the last time
+  __syncthreads();
+  constexpr int LPR = W / 16;   // 128-byte lines per tile row
+  for (int ln = threadIdx.x; ln < 2 * L2 * LPR; ln += kThreads) {
+    const int rr = ln / (L2 * LPR), rest = ln % (L2 * LPR);
+    discard_l2(scr + (size_t)(2 * rr) * M + (size_t)(rest / LPR) * L1 + (size_t)tile * W + (rest % LPR) * 16);
+  }
 }
 
 template <int M>
@@ -257,7 +275,7 @@ __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C
 
 // bounded wait until *c >= need (thread 0 only); false on timeout.  A wait
 // that was not satisfied at once adds its cycles to the header's counters.
-__device__ __forceinline__ bool wait_geq(const uint32_t* c, uint32_t need, WorkHeader* hdr) {
+__device__ __forceinline__ bool wait_geq(const uint32_t* c, uint32_t need, WorkHeader* hdr, long long limit) {
   const long long t0 = clock64();
   for (int it = 0;; ++it) {
     uint32_t v;
@@ -270,7 +288,7 @@ __device__ __forceinline__ bool wait_geq(const uint32_t* c, uint32_t need, WorkH
       }
       return true;
     }
-    if (dt > (1ll << 32)) return false;   // about two seconds
+    if (dt > limit) return false;
     __nanosleep(256);
   }
 }
@@ -296,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 2) fx_kernel(const __grid_constant__
       if (idx < (uint32_t)a.ntasks) {
         t = a.tasks[idx];
         next = atomicAdd(&a.hdr->counter, 1u);
-        if (t.widx >= 0 && !wait_geq(a.cnt + t.widx, t.wneed, a.hdr)) {
+        if (t.widx >= 0 && !wait_geq(a.cnt + t.widx, t.wneed, a.hdr, a.wait_limit)) {
           ok = 0;
           record_error(a.hdr, DC_ERR_TIMEOUT, (int)idx);
         }

@@ -145,3 +145,24 @@ def test_schedules_give_identical_results(dc):
     check_all(sizes, f, g, off, ref.cpu().numpy())
     fp64 = dc.BatchedPlan(sizes, dtype=torch.complex128)
     assert fp64.schedule() is None
+
+
+def test_bounded_wait_reports_timeout(dc):
+    # a dependency nothing satisfies: the kernel's bounded wait runs out
+    # after about a millisecond, records DC_ERR_TIMEOUT and the launch ends
+    import ctypes
+    from paper_1008_1366_gb300 import _native
+    L = _native.lib()
+    work = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.dc_selftest_wait_timeout(ctypes.c_void_p(work.data_ptr()), work.numel(), 2_000_000, s) == 0
+    torch.cuda.synchronize()
+    assert dc.read_status(work) == (5, 0)
+    # the context stays usable: an ordinary plan runs and is correct
+    sizes = [64, 65536]
+    _, f, g, off, h = run_plan(dc, sizes, 27)
+    check_all(sizes, f, g, off, h)
+    # argument checks
+    assert L.dc_selftest_wait_timeout(ctypes.c_void_p(work.data_ptr()), 100, 1000, s) == 6
+    assert L.dc_selftest_wait_timeout(ctypes.c_void_p(work.data_ptr() + 8), 4000, 1000, s) == 3
+    assert L.dc_selftest_wait_timeout(ctypes.c_void_p(0), 4096, 1000, s) == 1
