@@ -435,7 +435,26 @@ def main():
             worst64 = max(worst64, float(np.linalg.norm(h64[a:b] - ref) / np.linalg.norm(ref)))
         fp64 = {"convs_per_s": n_inst / (t64 / 1e3), "ms_per_batch": t64, "launches": plan64.launches,
                 "max_rel_l2_sampled": worst64, "tol": 1e-12}
-        del tf64, tg64, th64, w64, plan64
+        del w64, plan64
+        # the same FP64 arithmetic batched in one launch (context for the
+        # precision cost alone)
+        planb = dcl.BatchedPlan(ms, dtype=torch.complex128)
+        wb = planb.workspace(dev)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                planb(tf64, tg64, out=th64, work=wb)
+            e0.record(stream)
+            for _ in range(5):
+                planb(tf64, tg64, out=th64, work=wb)
+            e1.record(stream)
+        stream.synchronize()
+        tb = e0.elapsed_time(e1) / 5
+        hb = th64.cpu().numpy()
+        worstb = max(float(np.linalg.norm(hb[off[i]:off[i + 1]] - oracle.padded_complex(f[off[i]:off[i + 1]], g[off[i]:off[i + 1]]))
+                           / np.linalg.norm(oracle.padded_complex(f[off[i]:off[i + 1]], g[off[i]:off[i + 1]]))) for i in pick)
+        fp64["batched_one_launch"] = {"convs_per_s": n_inst / (tb / 1e3), "ms_per_batch": tb,
+                                      "max_rel_l2_sampled": worstb}
+        del tf64, tg64, th64, wb, planb
 
     cpu = None
     if not args.no_cpu and rank == 0:

@@ -184,11 +184,17 @@ dc_status dc_conv_hermitian_3d_adjoint(const void* w, const void* f, const void*
  * A plan fixes the sizes m[0..n-1] (host array), the dtype and the per-size
  * kernel configuration; instance i occupies elements [off_i, off_i + m_i) of
  * the packed arrays f, g, h with off_i = m_0 + ... + m_{i-1}.
- * flags: bit 0 = autotune the per-size configuration on the current device
- * (times candidates; needs the GPU idle), bit 1 = force the shared-memory-
- * resident path only where it fits, bit 2 = one launch per instance (the
- * "plain" comparison mode).  Planning allocates device memory; execution does
- * not.  dc_conv_complex_1d_batched may be captured in a CUDA graph.
+ * When every m lies in {2^a, 3*2^a, 5*2^a}, 64 <= m <= 65536, the plan runs
+ * on the fixed-shape engine (compile-time code per size; instances with
+ * m <= 256 E wholly in shared memory, larger ones as row/column passes
+ * through L2-resident scratch, all as tasks of one persistent queue);
+ * otherwise on the runtime-shaped engine.
+ * flags: DC_PLAN_AUTOTUNE = time candidates on the current device (the queue
+ * order of the fixed-shape engine, the per-size configuration of the
+ * runtime-shaped one; needs the GPU idle), DC_PLAN_ONE_PER_LAUNCH = one
+ * launch per instance, in instance order (the "plain" comparison mode).
+ * Planning allocates device memory; execution does not.
+ * dc_conv_complex_1d_batched may be captured in a CUDA graph.
  * ------------------------------------------------------------------------- */
 typedef struct dc_batched_plan dc_batched_plan;
 #define DC_PLAN_AUTOTUNE        1
@@ -206,8 +212,8 @@ dc_status dc_batched_plan_launches(const dc_batched_plan* plan, int32_t* launche
 dc_status dc_batched_plan_describe(const dc_batched_plan* plan, int32_t i, int64_t* m,
                                    int32_t* level, int32_t* nt, int32_t* l1, int32_t* l2,
                                    int32_t* w);
-/* Queue order of an FP32 plan on the fixed-shape engine (every size in the
- * set {2^a, 3*2^a, 5*2^a}, 64 <= m <= 65536): *batch_target = column tiles
+/* Queue order of a plan on the fixed-shape engine (every size in the set
+ * {2^a, 3*2^a, 5*2^a}, 64 <= m <= 65536; not the one-per-launch mode): *batch_target = column tiles
  * per batch of two-level instances (the pipeline distance between their
  * passes), *l1_mode = placement of the one-level work (0 after the
  * two-level pipeline, 1 the larger half spread over it, 2 before it).  No

@@ -16,8 +16,10 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdealias.so")
 
-SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu",
-           "fixed_batched.cu"]
+SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu"]
+# the fixed-shape engine, one translation unit per precision
+FIXED = [("fixed_batched_f.o", ["-DDC_FX_P=f32", "-DDC_FX_C=float2"]),
+         ("fixed_batched_d.o", ["-DDC_FX_P=f64", "-DDC_FX_C=double2"])]
 # the fused 1D kernel, one translation unit per (kind, precision)
 INSTANCES = [(k, tag, c) for k in range(6) for tag, c in (("f", "float2"), ("d", "double2"))]
 
@@ -27,6 +29,8 @@ def _units():
     for k, tag, c in INSTANCES:
         units.append(("conv1d_inst.cu", f"conv1d_k{k}_{tag}.o",
                       [f"-DDC_INST_KIND={k}", f"-DDC_INST_C={c}", f"-DDC_INST_TAG={tag}"]))
+    for obj, defs in FIXED:
+        units.append(("fixed_batched.cu", obj, defs))
     return units
 
 

@@ -1,9 +1,10 @@
 // Batched 1D complex convolutions of uneven sizes in one persistent launch.
 //
-// FP32 batches whose sizes all lie in the set {2^a, 3*2^a, 5*2^a} in
-// [64, 65536] run on the fixed-shape engine (fixed.cuh, fixed_batched.cu):
-// a task queue of level-1 groups and level-2 pass tasks.  Other batches
-// run on the runtime-shaped engine (conv1d.cuh), as follows.
+// Batches whose sizes all lie in the set {2^a, 3*2^a, 5*2^a} in [64, 65536]
+// run on the fixed-shape engine (fixed.cuh, fixed_batched.cu; FP32 and FP64
+// builds): a task queue of level-1 groups and level-2 pass tasks, one launch
+// (or, in the plain mode, one launch per instance).  Other batches run on
+// the runtime-shaped engine (conv1d.cuh), as follows.
 //
 // Planning groups the instances by size; each size gets a configuration
 // (level 1: `nt` instances per block wholly in shared memory; level 2: one
@@ -42,14 +43,32 @@ struct dc_batched_plan {
   size_t slot = 0, work = 0;
   // fixed-shape engine
   bool fx = false;
+  const struct FxOps* ops = nullptr;
   fx::HostPlan hp;
   fx::Task* d_tasks = nullptr;
   fx::L2Inst* d_l2 = nullptr;
-  const float2* tabs[fx::kNumSizes] = {};
+  const void* tabs[fx::kNumSizes] = {};
   size_t cnt_bytes = 0;   // header + counters, zeroed before each launch
   fx::Schedule fx_sched{0, 0};   // queue order of the fixed engine
   std::vector<int64_t> off_host;
+  // plain mode: one launch per instance over its own task range
+  std::vector<int32_t> inst_first, inst_count;
 };
+
+// one precision of the fixed-shape engine
+struct FxOps {
+  int (*size_code)(int64_t);
+  int64_t (*code_size)(int);
+  void (*code_shape)(int, int*, int*, int*, int*, int*);
+  int (*code_smem)(int);
+  bool (*build_plan)(const int64_t*, int32_t, const int64_t*, const fx::Schedule&, fx::HostPlan*);
+  dc_status (*prepare_kernel)(int, int*);
+  dc_status (*launch)(const fx::FxArgs&, int, int, cudaStream_t);
+};
+static const FxOps kFx32{fx::f32::size_code, fx::f32::code_size,   fx::f32::code_shape, fx::f32::code_smem,
+                         fx::f32::build_plan, fx::f32::prepare_kernel, fx::f32::launch};
+static const FxOps kFx64{fx::f64::size_code, fx::f64::code_size,   fx::f64::code_shape, fx::f64::code_smem,
+                         fx::f64::build_plan, fx::f64::prepare_kernel, fx::f64::launch};
 
 namespace {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -143,7 +162,7 @@ dc_status autotune_size(int64_t m, int count, int ds, int smem_max, CfgDev* best
   return DC_OK;
 }
 size_t fx_work_bytes(const dc_batched_plan* p) {
-  return p->cnt_bytes + p->hp.scratch * sizeof(float2);
+  return p->cnt_bytes + p->hp.scratch * (size_t)p->ds;
 }
 
 dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
@@ -170,12 +189,11 @@ dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
   return DC_OK;
 }
 
-dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work, cudaStream_t s) {
-  DC_CUDA_TRY(cudaMemsetAsync(work, 0, p->cnt_bytes, s));
+fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work) {
   fx::FxArgs a{};
-  a.f = (const float2*)f;
-  a.g = (const float2*)g;
-  a.h = (float2*)h;
+  a.f = f;
+  a.g = g;
+  a.h = h;
   a.off = p->d_off;
   a.order = p->d_order;
   a.tasks = p->d_tasks;
@@ -183,16 +201,33 @@ dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void
   a.l2 = p->d_l2;
   a.hdr = (WorkHeader*)work;
   a.cnt = (uint32_t*)((char*)work + sizeof(WorkHeader));
-  a.scratch = (float2*)((char*)work + p->cnt_bytes);
+  a.scratch = (char*)work + p->cnt_bytes;
   a.wait_limit = fx::kWaitLimit;
   for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
-  return fx::launch(a, p->grid, p->smem, s);
+  return a;
+}
+
+dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work, cudaStream_t s) {
+  DC_CUDA_TRY(cudaMemsetAsync(work, 0, p->cnt_bytes, s));
+  fx::FxArgs a = fx_args(p, f, g, h, work);
+  if (p->inst_first.empty()) return p->ops->launch(a, p->grid, p->smem, s);
+  // plain mode: each instance's tasks in a launch of their own (the queue
+  // counter is reset before each; the dependency counters are distinct)
+  const fx::Task* base = a.tasks;
+  for (size_t i = 0; i < p->inst_first.size(); ++i) {
+    if (i > 0) DC_CUDA_TRY(cudaMemsetAsync(&((WorkHeader*)work)->counter, 0, sizeof(uint32_t), s));
+    a.tasks = base + p->inst_first[i];
+    a.ntasks = p->inst_count[i];
+    dc_status st = p->ops->launch(a, std::min(p->grid, (int)a.ntasks), p->smem, s);
+    if (st != DC_OK) return st;
+  }
+  return DC_OK;
 }
 
 // Times the whole batch on scratch buffers (median of three after a warm-up, ms).
-float fx_time(dc_batched_plan* p, const std::vector<int64_t>& off, cudaStream_t s) {
+float fx_time(dc_batched_plan* p, cudaStream_t s) {
   DevBuf f, g, h, w;
-  const size_t bytes = (size_t)p->total * sizeof(float2);
+  const size_t bytes = (size_t)p->total * (size_t)p->ds;
   if (cudaMalloc(&f.p, bytes) != cudaSuccess || cudaMalloc(&g.p, bytes) != cudaSuccess ||
       cudaMalloc(&h.p, bytes) != cudaSuccess || cudaMalloc(&w.p, p->work) != cudaSuccess)
     return -1;
@@ -220,48 +255,85 @@ float fx_time(dc_batched_plan* p, const std::vector<int64_t>& off, cudaStream_t 
   return t[1];
 }
 
+// Plain mode: the queues of one-instance plans, concatenated in instance
+// order, each launched on its own.  They run one after another, so they
+// share one scratch region.
+bool fx_build_plain(dc_batched_plan* p, const int64_t* m, int32_t n, const std::vector<int64_t>& off) {
+  fx::HostPlan all;
+  p->inst_first.clear();
+  p->inst_count.clear();
+  const fx::Schedule sc{p->grid / 2, 0};
+  for (int32_t i = 0; i < n; ++i) {
+    fx::HostPlan one;
+    if (!p->ops->build_plan(m + i, 1, off.data() + i, sc, &one)) return false;
+    const int32_t ob = (int32_t)all.order.size(), lb = (int32_t)all.l2.size(), cb = (int32_t)all.ncnt;
+    p->inst_first.push_back((int32_t)all.tasks.size());
+    p->inst_count.push_back((int32_t)one.tasks.size());
+    for (fx::Task t : one.tasks) {
+      if ((t.kc >> 8) == fx::T_L1) t.a += ob;
+      else t.a += lb;
+      if (t.widx >= 0) t.widx += cb;
+      if (t.sidx >= 0) t.sidx += cb;
+      all.tasks.push_back(t);
+    }
+    for (int32_t id : one.order) all.order.push_back(id + i);   // the one-instance plan numbers it 0
+    all.l2.insert(all.l2.end(), one.l2.begin(), one.l2.end());
+    all.ncnt += one.ncnt;
+    all.scratch = std::max(all.scratch, one.scratch);
+    all.smem = std::max(all.smem, one.smem);
+    for (int c : one.codes)
+      if (std::find(all.codes.begin(), all.codes.end(), c) == all.codes.end()) all.codes.push_back(c);
+  }
+  std::sort(all.codes.begin(), all.codes.end());
+  p->hp = std::move(all);
+  return true;
+}
+
 dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const std::vector<int64_t>& off,
                        int32_t flags) {
   p->fx = true;
+  p->ops = p->ds == 8 ? &kFx32 : &kFx64;
   p->off_host = off;
   int bps = 0;
   // kernel attributes for the largest shared-memory need of any size
   int smem_all = 0;
-  for (int c = 0; c < fx::kNumSizes; ++c) smem_all = std::max(smem_all, fx::code_smem(c));
-  dc_status st = fx::prepare_kernel(smem_all, &bps);
+  for (int c = 0; c < fx::kNumSizes; ++c) smem_all = std::max(smem_all, p->ops->code_smem(c));
+  dc_status st = p->ops->prepare_kernel(smem_all, &bps);
   if (st != DC_OK) return st;
   p->grid = bps * device_info().sms;
   const fx::Schedule dflt{p->grid / 2, 0};
-  if (!fx::build_plan(m, n, off.data(), dflt, &p->hp)) return DC_ERR_SIZE;
+  const bool plain = (flags & DC_PLAN_ONE_PER_LAUNCH) != 0;
+  if (plain ? !fx_build_plain(p, m, n, off) : !p->ops->build_plan(m, n, off.data(), dflt, &p->hp))
+    return DC_ERR_SIZE;
   p->smem = p->hp.smem;
   for (int c : p->hp.codes) {
     const void* tw = nullptr;
-    st = get_root_table(2 * fx::code_size(c), 8, &tw);
+    st = get_root_table(2 * p->ops->code_size(c), p->ds, &tw);
     if (st != DC_OK) return st;
-    p->tabs[c] = (const float2*)tw;
+    p->tabs[c] = tw;
   }
   st = fx_upload(p, off);
   if (st != DC_OK) return st;
   p->fx_sched = dflt;
-  if (flags & DC_PLAN_AUTOTUNE) {
+  if ((flags & DC_PLAN_AUTOTUNE) && !plain) {
     // the queue order: pipeline distance between the level-2 passes (waits
     // against scratch footprint in L2) and the placement of level-1 work
     cudaStream_t s;
     DC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     fx::Schedule best = dflt;
-    float tbest = fx_time(p, off, s);
+    float tbest = fx_time(p, s);
     for (int cand : {p->grid / 4, p->grid / 2, p->grid}) {
       for (int mode = 0; mode < fx::kL1Modes; ++mode) {
         const fx::Schedule sc{cand, mode};
         if (cand < 1 || (cand == dflt.batch_target && mode == dflt.l1_mode)) continue;
-        if (!fx::build_plan(m, n, off.data(), sc, &p->hp) || fx_upload(p, off) != DC_OK) continue;
-        const float t = fx_time(p, off, s);
+        if (!p->ops->build_plan(m, n, off.data(), sc, &p->hp) || fx_upload(p, off) != DC_OK) continue;
+        const float t = fx_time(p, s);
         if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; best = sc; }
       }
     }
     cudaStreamDestroy(s);
     cudaGetLastError();
-    if (!fx::build_plan(m, n, off.data(), best, &p->hp)) return DC_ERR_SIZE;
+    if (!p->ops->build_plan(m, n, off.data(), best, &p->hp)) return DC_ERR_SIZE;
     st = fx_upload(p, off);
     if (st != DC_OK) return st;
     p->fx_sched = best;
@@ -292,8 +364,8 @@ dc_status dc_batched_plan_create(const int64_t* m, int32_t n, int32_t dtype, int
   }
   p->total = off[n];
 
-  bool all_fixed = ds == 8 && !one;
-  for (int32_t i = 0; i < n && all_fixed; ++i) all_fixed = fx::size_code(m[i]) >= 0;
+  bool all_fixed = true;
+  for (int32_t i = 0; i < n && all_fixed; ++i) all_fixed = fx::f32::size_code(m[i]) >= 0;
   if (all_fixed) {
     dc_status st = create_fixed(p, m, n, off, flags);
     if (st != DC_OK) { delete p; return st; }
@@ -375,7 +447,8 @@ dc_status dc_batched_plan_workspace_size(const dc_batched_plan* p, size_t* bytes
 
 dc_status dc_batched_plan_launches(const dc_batched_plan* p, int32_t* launches) {
   if (!p || !launches) return DC_ERR_ARG;
-  *launches = (!p->fx && (p->flags & DC_PLAN_ONE_PER_LAUNCH)) ? (int32_t)p->items.size() : 1;
+  if (p->fx) *launches = p->inst_first.empty() ? 1 : (int32_t)p->inst_first.size();
+  else *launches = (p->flags & DC_PLAN_ONE_PER_LAUNCH) ? (int32_t)p->items.size() : 1;
   return DC_OK;
 }
 
@@ -388,8 +461,8 @@ dc_status dc_selftest_wait_timeout(void* work, size_t work_bytes, int64_t cycles
   cudaStream_t s = (cudaStream_t)stream;
   int bps = 0;
   int smem = 0;
-  for (int c = 0; c < fx::kNumSizes; ++c) smem = std::max(smem, fx::code_smem(c));
-  dc_status st = fx::prepare_kernel(smem, &bps);
+  for (int c = 0; c < fx::kNumSizes; ++c) smem = std::max(smem, fx::f32::code_smem(c));
+  dc_status st = fx::f32::prepare_kernel(smem, &bps);
   if (st != DC_OK) return st;
   static const fx::Task task{(fx::T_B << 8) | 0, 0, 0, 0, 1u, -1};
   char* w = (char*)work;
@@ -402,22 +475,23 @@ dc_status dc_selftest_wait_timeout(void* work, size_t work_bytes, int64_t cycles
   a.cnt = (uint32_t*)(w + 256);
   a.wait_limit = cycles;
   // one block: it takes the task, waits, records the timeout and leaves
-  return fx::launch(a, 1, fx::code_smem(0), s);
+  return fx::f32::launch(a, 1, fx::f32::code_smem(0), s);
 }
 
 dc_status dc_batched_plan_schedule(const dc_batched_plan* p, int32_t* batch_target, int32_t* l1_mode) {
-  if (!p || !p->fx) return DC_ERR_ARG;
+  if (!p || !p->fx || !p->inst_first.empty()) return DC_ERR_ARG;
   if (batch_target) *batch_target = p->fx_sched.batch_target;
   if (l1_mode) *l1_mode = p->fx_sched.l1_mode;
   return DC_OK;
 }
 
 dc_status dc_batched_plan_set_schedule(dc_batched_plan* p, int32_t batch_target, int32_t l1_mode) {
-  if (!p || !p->fx || batch_target < 1 || l1_mode < 0 || l1_mode >= fx::kL1Modes) return DC_ERR_ARG;
+  if (!p || !p->fx || !p->inst_first.empty() || batch_target < 1 || l1_mode < 0 || l1_mode >= fx::kL1Modes)
+    return DC_ERR_ARG;
   std::vector<int64_t> ms(p->n);
   for (int32_t i = 0; i < p->n; ++i) ms[i] = p->off_host[i + 1] - p->off_host[i];
   const fx::Schedule sc{batch_target, l1_mode};
-  if (!fx::build_plan(ms.data(), p->n, p->off_host.data(), sc, &p->hp)) return DC_ERR_SIZE;
+  if (!p->ops->build_plan(ms.data(), p->n, p->off_host.data(), sc, &p->hp)) return DC_ERR_SIZE;
   dc_status st = fx_upload(p, p->off_host);
   if (st != DC_OK) return st;
   p->fx_sched = sc;
@@ -429,8 +503,8 @@ dc_status dc_batched_plan_describe(const dc_batched_plan* p, int32_t i, int64_t*
   if (p && p->fx) {
     if (i < 0 || i >= (int32_t)p->hp.codes.size()) return DC_ERR_ARG;
     int lv, per, a, b, ww;
-    fx::code_shape(p->hp.codes[i], &lv, &per, &a, &b, &ww);
-    if (m) *m = fx::code_size(p->hp.codes[i]);
+    p->ops->code_shape(p->hp.codes[i], &lv, &per, &a, &b, &ww);
+    if (m) *m = p->ops->code_size(p->hp.codes[i]);
     if (level) *level = lv;
     if (nt) *nt = per;
     if (l1) *l1 = a;

@@ -39,13 +39,23 @@
 
 #include "fft2.cuh"
 
+// The engine is compiled once per precision: DC_FX_P names the namespace
+// (f32 / f64) and DC_FX_C the complex type (float2 / double2).
+#ifndef DC_FX_P
+#define DC_FX_P f32
+#define DC_FX_C float2
+#endif
+
 namespace dc {
 namespace fx {
+namespace DC_FX_P {
 
-constexpr int kThreads = 256;       // threads per block; two blocks per SM
+constexpr int kThreads = 256;    // threads per block (FP32: two blocks per SM, FP64: one)
 constexpr int kRootsMax = 768;   // shared-memory root entries reserved (2m <= 131072)
 
-using C = float2;
+using C = DC_FX_C;
+using Real = decltype(C{}.x);
+constexpr bool kDouble = sizeof(C) == 16;
 
 // ---------------------------------------------------------------------------
 // compile-time plans
@@ -157,11 +167,14 @@ __device__ __forceinline__ C mul_root(C x, int sgn) {
   } else if constexpr (4 * k == R) {
     return si(x, sgn);
   } else if constexpr (2 * k == R) {
-    return make_float2(-x.x, -x.y);
+    C y;
+    y.x = -x.x;
+    y.y = -x.y;
+    return y;
   } else if constexpr (4 * k == 3 * R) {
     return si(x, -sgn);
   } else {
-    constexpr float c = (float)RootConst<R>::c[k], s = (float)RootConst<R>::s[k];
+    constexpr Real c = (Real)RootConst<R>::c[k], s = (Real)RootConst<R>::s[k];
     return mcs(x, c, s, sgn);
   }
 }
@@ -457,5 +470,6 @@ __device__ __forceinline__ void column(C* v, int i, C* Dp, const Roots<C>& rt, c
     for (int q = 0; q < K::R; ++q) st(pos<L, E, n - 1, FWD>(i, b, q), b * K::R + q, v[b * K::R + q]);
 }
 
+}  // namespace DC_FX_P
 }  // namespace fx
 }  // namespace dc

@@ -35,10 +35,11 @@ struct L2Inst {
   int64_t scr;   // element offset of its four m-element scratch arrays
 };
 
+// data pointers are float2 (FP32 engine) or double2 (FP64 engine)
 struct FxArgs {
-  const float2* f;
-  const float2* g;
-  float2* h;
+  const void* f;
+  const void* g;
+  void* h;
   const int64_t* off;      // per-instance element offsets
   const int32_t* order;    // instance ids of the level-1 tasks
   const Task* tasks;
@@ -47,21 +48,10 @@ struct FxArgs {
   const L2Inst* l2;
   uint32_t* cnt;           // dependency counters, zero before each launch
   WorkHeader* hdr;         // status word and queue counter, zero before each launch
-  float2* scratch;
+  void* scratch;
   long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
-  const float2* tab[kNumSizes];   // root tables zeta_{2m}^i, i < 2m, per size code
+  const void* tab[kNumSizes];     // root tables zeta_{2m}^i, i < 2m, per size code
 };
-
-constexpr long long kWaitLimit = 1ll << 32;   // about two seconds at 2 GHz
-
-// size code of m, or -1 when m is not in the set
-int size_code(int64_t m);
-int64_t code_size(int code);
-bool code_level1(int code);
-// instances per task (level 1) or the level-2 split of a size code
-void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W);
-// dynamic shared memory the kernel needs for a size code
-int code_smem(int code);
 
 struct HostPlan {
   std::vector<Task> tasks;
@@ -83,14 +73,27 @@ struct Schedule {
   int l1_mode;
 };
 constexpr int kL1Modes = 3;
+constexpr long long kWaitLimit = 1ll << 32;   // about two seconds at 2 GHz
 
-// Builds the task queue for n instances of sizes m[i] at element offsets
-// off[i] (all sizes must have a code).
-bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc, HostPlan* out);
+// The interface of one precision of the engine (namespaces f32 and f64).
+#define DC_FX_DECLARE                                                                       \
+  /* size code of m, or -1 when m is not in the set */                                      \
+  int size_code(int64_t m);                                                                 \
+  int64_t code_size(int code);                                                              \
+  /* instances per task (level 1) or the level-2 split of a size code */                    \
+  void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W);           \
+  /* dynamic shared memory the kernel needs for a size code */                              \
+  int code_smem(int code);                                                                  \
+  /* the task queue for n instances of sizes m[i] at element offsets off[i] */              \
+  bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc,     \
+                  HostPlan* out);                                                           \
+  /* kernel attributes, occupancy */                                                        \
+  dc_status prepare_kernel(int smem, int* blocks_per_sm);                                   \
+  dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s);
 
-// kernel attributes, occupancy
-dc_status prepare_kernel(int smem, int* blocks_per_sm);
-dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s);
+namespace f32 { DC_FX_DECLARE }
+namespace f64 { DC_FX_DECLARE }
+#undef DC_FX_DECLARE
 
 }  // namespace fx
 }  // namespace dc

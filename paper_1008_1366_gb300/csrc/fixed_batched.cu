@@ -29,6 +29,7 @@
 
 namespace dc {
 namespace fx {
+namespace DC_FX_P {
 
 // Drops a 128-byte line of dead scratch from L2 without writing it back to
 // HBM (the data were read for the last time; the next user overwrites
@@ -57,6 +58,8 @@ static_assert(roots_count(131072) <= kRootsMax, "root table fits its reservation
 static_assert(roots_count(98304) <= kRootsMax, "root table fits its reservation");
 static_assert(roots_count(81920) <= kRootsMax, "root table fits its reservation");
 
+constexpr int kBlocksPerSM = kDouble ? 1 : 2;
+
 template <int M> struct Shape {
   static constexpr bool l1 = is_level1(M);
   // level 1
@@ -77,12 +80,14 @@ template <int M> struct Shape {
   static constexpr int EC = l1 ? 16 : col_E(M);
   static_assert(l1 || (L1 % W == 0 && (2 * L2) % GR == 0 && L1 * L2 == M), "level-2 tiling must be exact");
   static_assert(!l1 || kThreads % T == 0, "level-1 groups must tile the block");
-  static constexpr int smem = l1 ? G * group_stride(M, T) * 8
-                                 : (GR * group_stride(L1, T1) * 8 > W * L2 * 8 ? GR * group_stride(L1, T1) * 8
-                                                                                 : W * L2 * 8);
-  // two blocks per SM: 228 KB per SM less 1 KB reserved per block and the
-  // static shared variables
-  static_assert(smem + kRootsMax * 8 <= (233472 - 2 * 1024) / 2 - 64, "two blocks fit on an SM");
+  static constexpr int CB = (int)sizeof(C);
+  static constexpr int smem = l1 ? G * group_stride(M, T) * CB
+                                 : (GR * group_stride(L1, T1) * CB > W * L2 * CB ? GR * group_stride(L1, T1) * CB
+                                                                                   : W * L2 * CB);
+  // FP32: two blocks per SM, FP64: one (228 KB per SM less 1 KB reserved per
+  // block and the static shared variables)
+  static_assert(smem + kRootsMax * CB <= (233472 - kBlocksPerSM * 1024) / kBlocksPerSM - 64,
+                "the blocks fit on an SM");
 };
 
 // ---------------------------------------------------------------------------
@@ -99,16 +104,18 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
   const int gi = threadIdx.x / T, i = threadIdx.x % T;
   const bool act = gi < count;
   const int64_t off = act ? a->off[a->order[first + gi]] : 0;
-  const C* f = a->f + off;
-  const C* g = a->g + off;
-  C* h = a->h + off;
+  const C* f = (const C*)a->f + off;
+  const C* g = (const C*)a->g + off;
+  C* h = (C*)a->h + off;
   C* A = sm + gi * GS;
   C* B = A + PL;
-  const float sc = 1.0f / (float)(2 * M);
+  const Real sc = (Real)1 / (Real)(2 * M);
   const GroupSync<T> sync{1 + gi};
   // groups past `count` transform zeros and store nothing: the stages
   // themselves carry no condition
-  const C zero = make_float2(0.f, 0.f);
+  C zero;
+  zero.x = 0;
+  zero.y = 0;
   if constexpr (R == 0) {
     // residue 0 (Eq. (2.1) with r = 0): partial output
     conv_residue<M, E, TN>(
@@ -157,7 +164,7 @@ __device__ __noinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, Root
   const int c = threadIdx.x % W, i = threadIdx.x / W;
   const int k1 = tile * W + c;
   const L2Inst in = a->l2[l];
-  C* scr = a->scratch + in.scr;
+  C* scr = (C*)a->scratch + in.scr;
   // residue-1 input twiddles zeta_{2m}^{k1 + L1 k2}, shared by f and g
   C tw[E];
 #pragma unroll
@@ -166,7 +173,7 @@ __device__ __noinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, Root
     for (int q = 0; q < K::R; ++q) tw[b * K::R + q] = rt.at(k1 + L1 * pos<L2, E, 0, false>(i, b, q));
 #pragma unroll 1
   for (int arr = 0; arr < 2; ++arr) {
-    const C* x = (arr ? a->g : a->f) + in.off + k1;
+    const C* x = (const C*)(arr ? a->g : a->f) + in.off + k1;
     C raw[E];
 #pragma unroll
     for (int b = 0; b < K::NB; ++b)
@@ -194,7 +201,7 @@ __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Root
   const int gi = threadIdx.x / T1, i = threadIdx.x % T1;
   const int row = unit * GR + gi;
   const int r = row / L2, j2 = row % L2;
-  C* scr = a->scratch + a->l2[l].scr;
+  C* scr = (C*)a->scratch + a->l2[l].scr;
   C* sf = scr + (size_t)(2 * r) * M + (size_t)j2 * L1;
   const C* sg = scr + (size_t)(2 * r + 1) * M + (size_t)j2 * L1;
   C* A = sm + gi * GS;
@@ -220,7 +227,7 @@ __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Root
   }
   // the g row was read for the last time (every thread of the group loaded
   // its part before the group's first barrier)
-  for (int ln = i; ln < L1 / 16; ln += T1) discard_l2(sg + ln * 16);
+  for (int ln = i; ln < L1 * (int)sizeof(C) / 128; ln += T1) discard_l2((const char*)sg + ln * 128);
 }
 
 // pass C: column tile `tile` of level-2 instance l, both residues, output
@@ -232,9 +239,9 @@ __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Root
   const int c = threadIdx.x % W, i = threadIdx.x / W;
   const int k1 = tile * W + c;
   const L2Inst in = a->l2[l];
-  const C* scr = a->scratch + in.scr;
-  C* h = a->h + in.off + k1;
-  const float sc = 1.0f / (float)(2 * M);
+  const C* scr = (const C*)a->scratch + in.scr;
+  C* h = (C*)a->h + in.off + k1;
+  const Real sc = (Real)1 / (Real)(2 * M);
   C y0[E];
   C vin[2][E];
 #pragma unroll
@@ -253,10 +260,11 @@ __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Root
   });
   // both residues' product columns of the tile were read for the last time
   __syncthreads();
-  constexpr int LPR = W / 16;   // 128-byte lines per tile row
+  constexpr int LPR = W * (int)sizeof(C) / 128;   // 128-byte lines per tile row
   for (int ln = threadIdx.x; ln < 2 * L2 * LPR; ln += kThreads) {
     const int rr = ln / (L2 * LPR), rest = ln % (L2 * LPR);
-    discard_l2(scr + (size_t)(2 * rr) * M + (size_t)(rest / LPR) * L1 + (size_t)tile * W + (rest % LPR) * 16);
+    const C* row = scr + (size_t)(2 * rr) * M + (size_t)(rest / LPR) * L1 + (size_t)tile * W;
+    discard_l2((const char*)row + (rest % LPR) * 128);
   }
 }
 
@@ -293,7 +301,7 @@ __device__ __forceinline__ bool wait_geq(const uint32_t* c, uint32_t need, WorkH
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) fx_kernel(const __grid_constant__ FxArgs a) {
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid_constant__ FxArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* rts = (C*)smem_raw;
   C* sm = rts + kRootsMax;
@@ -330,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 2) fx_kernel(const __grid_constant__
       // lo = zeta_TN^b (b < 2^sh), hi = zeta_TN^(a 2^sh), from the full table
       const int TN = 2 * size_of_code(code);
       const int sh = roots_sh(TN), nlo = 1 << sh, cnt = roots_count(TN);
-      const C* tab = a.tab[code];
+      const C* tab = (const C*)a.tab[code];
       for (int e = threadIdx.x; e < cnt; e += kThreads) rts[e] = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
       rt = Roots<C>{rts, rts + nlo, sh, nlo - 1};
       cur = code;
@@ -390,7 +398,7 @@ int size_code(int64_t m) {
 }
 int64_t code_size(int code) { return size_of_code(code); }
 bool code_level1(int code) { return tables().lvl[code] == 1; }
-int code_smem(int code) { return tables().smem[code] + kRootsMax * 8; }
+int code_smem(int code) { return tables().smem[code] + kRootsMax * (int)sizeof(C); }
 void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W) {
   const Tables& t = tables();
   *level = t.lvl[code];
@@ -543,5 +551,6 @@ dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s) {
   return DC_OK;
 }
 
+}  // namespace DC_FX_P
 }  // namespace fx
 }  // namespace dc

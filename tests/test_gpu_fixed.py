@@ -1,19 +1,20 @@
-"""GPU parity of the fixed-shape FP32 engine (batched plans whose sizes all lie
-in {2^a, 3*2^a, 5*2^a}, 64 <= m <= 65536) against the FP64 oracle, through
-the C ABI.
+"""GPU parity of the fixed-shape engine (batched plans whose sizes all lie in
+{2^a, 3*2^a, 5*2^a}, 64 <= m <= 65536; FP32 and FP64 builds) against the FP64
+oracle, through the C ABI.
 
 Covers every size of the set (both levels, every radix), partial level-1
 groups, level-2 instances spread over more batches than there are scratch
 regions (so regions are reused behind the dependency counters), the
 pipeline-distance settings the autotuner picks from, and the status word
-after each launch.  Bar: relative L2 <= 5e-7 log2(2m) per instance."""
+after each launch.  Bars per instance: relative L2 <= 5e-7 log2(2m) (FP32),
+<= 1e-12 (FP64)."""
 
 import numpy as np
 import pytest
 import torch
 
 import oracle
-from conftest import fp32_tol, rel_l2
+from conftest import FP64_TOL, fp32_tol, rel_l2
 from paper_1008_1366_gb300 import synthetic
 
 pytestmark = pytest.mark.gpu
@@ -25,11 +26,18 @@ def dc():
     return dc
 
 
-def run_plan(dc, sizes, seed, flags=0):
+DTYPES = [torch.complex64, torch.complex128]
+
+
+def tol(dtype, m):
+    return fp32_tol(2 * m) if dtype == torch.complex64 else FP64_TOL
+
+
+def run_plan(dc, sizes, seed, flags=0, dtype=torch.complex64):
     f, g, off = synthetic.batched_inputs(sizes, seed)
-    plan = dc.BatchedPlan(sizes, dtype=torch.complex64, flags=flags)
-    tf = torch.tensor(f, dtype=torch.complex64, device="cuda")
-    tg = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    plan = dc.BatchedPlan(sizes, dtype=dtype, flags=flags)
+    tf = torch.tensor(f, dtype=dtype, device="cuda")
+    tg = torch.tensor(g, dtype=dtype, device="cuda")
     work = plan.workspace(tf.device)
     h = plan(tf, tg, work=work)
     torch.cuda.synchronize()
@@ -37,20 +45,21 @@ def run_plan(dc, sizes, seed, flags=0):
     return plan, f, g, off, h.cpu().numpy()
 
 
-def check_all(sizes, f, g, off, h):
+def check_all(sizes, f, g, off, h, dtype=torch.complex64):
     worst = 0.0
     for i, m in enumerate(sizes):
         a, b = off[i], off[i + 1]
         ref = oracle.padded_complex(f[a:b], g[a:b])
         e = rel_l2(h[a:b], ref)
-        worst = max(worst, e / fp32_tol(2 * m))
-        assert e <= fp32_tol(2 * m), (i, m, e)
+        worst = max(worst, e / tol(dtype, m))
+        assert e <= tol(dtype, m), (i, m, e)
     return worst
 
 
-def test_every_size_once(dc):
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_every_size_once(dc, dtype):
     sizes = list(synthetic.SIZES_31)
-    plan, f, g, off, h = run_plan(dc, sizes, 21)
+    plan, f, g, off, h = run_plan(dc, sizes, 21, dtype=dtype)
     assert plan.launches == 1
     desc = plan.describe()
     assert sorted(d[0] for d in desc) == sorted(sizes)
@@ -62,25 +71,37 @@ def test_every_size_once(dc):
         fam = sorted(m for m in sizes if m % base == 0 and (m // base) & (m // base - 1) == 0)
         lv = [levels[m] for m in fam]
         assert lv == sorted(lv)
-    check_all(sizes, f, g, off, h)
+    check_all(sizes, f, g, off, h, dtype)
 
 
-def test_partial_groups_and_order(dc):
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_partial_groups_and_order(dc, dtype):
     # level-1 groups that are full, partial and single; sizes interleaved
     sizes = [64] * 130 + [96] * 3 + [4096] * 3 + [80, 160, 320] * 5 + [8192, 12288, 10240] * 2
     rng = np.random.default_rng(3)
     sizes = [sizes[i] for i in rng.permutation(len(sizes))]
-    _, f, g, off, h = run_plan(dc, sizes, 22)
-    check_all(sizes, f, g, off, h)
+    _, f, g, off, h = run_plan(dc, sizes, 22, dtype=dtype)
+    check_all(sizes, f, g, off, h, dtype)
 
 
-def test_level2_region_reuse(dc):
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_level2_region_reuse(dc, dtype):
     # many level-2 instances: more batches than the four scratch regions
     sizes = [65536] * 24 + [16384] * 30 + [49152] * 6 + [20480] * 8 + [2048] * 20
     rng = np.random.default_rng(4)
     sizes = [sizes[i] for i in rng.permutation(len(sizes))]
-    _, f, g, off, h = run_plan(dc, sizes, 23)
-    check_all(sizes, f, g, off, h)
+    _, f, g, off, h = run_plan(dc, sizes, 23, dtype=dtype)
+    check_all(sizes, f, g, off, h, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_one_per_launch(dc, dtype):
+    # the plain mode: one launch per instance, each over its own task range
+    sizes = [65536, 64, 12288, 640, 40960, 96, 4096]
+    plan, f, g, off, h = run_plan(dc, sizes, 28, flags=4, dtype=dtype)
+    assert plan.launches == len(sizes)
+    assert plan.schedule() is None
+    check_all(sizes, f, g, off, h, dtype)
 
 
 def test_autotuned_plan_matches(dc):
@@ -143,8 +164,8 @@ def test_schedules_give_identical_results(dc):
             assert dc.read_status(work) == (0, 0)
             assert torch.equal(h, ref), (target, mode)
     check_all(sizes, f, g, off, ref.cpu().numpy())
-    fp64 = dc.BatchedPlan(sizes, dtype=torch.complex128)
-    assert fp64.schedule() is None
+    other = dc.BatchedPlan(sizes + [48], dtype=torch.complex64)   # 48 < 64: runtime-shaped engine
+    assert other.schedule() is None
 
 
 def test_bounded_wait_reports_timeout(dc):
