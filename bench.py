@@ -388,6 +388,11 @@ def main():
         t_ms = float(t.item())
         if pg:
             pg.barrier()
+    # where the kernel's blocks spent their cycles (last launch of the loop)
+    trace = dcl.read_trace(work)
+    busy = sum(trace["cycles"].values())
+    trace = {"tasks": trace["tasks"], "cycle_share": {k: round(v / max(1, busy), 4) for k, v in trace["cycles"].items()},
+             "tasks_that_waited": trace["waited"], "wait_cycles_over_task_cycles": round(trace["wait_cycles"] / max(1, busy), 5)}
     convs_total = n_inst * world * args.steps
     value = convs_total / (t_ms / 1e3)
     ms_step = t_ms / args.steps
@@ -487,6 +492,7 @@ def main():
             "parity": {"max_rel_l2_sampled": worst, "worst_err_over_tol": worst_ratio,
                        "tol": "5e-7*log2(2m)", "instances_checked": len(pick)},
             "fp64_plain": fp64,
+            "trace": trace,
         }
         print(json.dumps(line), flush=True)
     if pg:

@@ -83,6 +83,14 @@ dc_status dc_prepare(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dt
  * was last cleared by an entry point; *detail = kernel-specific detail. */
 dc_status dc_read_status(const void* work, void* stream, int32_t* status, int32_t* detail);
 
+/* Trace counters of the last batched launch on the fixed-shape engine
+ * (workspace header), after synchronizing `stream`; no counterpart in the
+ * paper.  out[0] = tasks that found their dependency unmet, out[1] = SM
+ * cycles they waited, out[2..5] = SM cycles spent in level-1 tasks and in
+ * the tasks of passes A, B, C, out[6..9] = the number of such tasks.  Other
+ * kernels leave them zero. */
+dc_status dc_read_trace(const void* work, void* stream, uint64_t* out);
+
 /* ---------------------------------------------------------------------------
  * 1D complex binary convolution (Sec. 2.1, Eqs. (2.1)-(2.2), Function cconv).
  * f, g: m complex values, Fourier origin at index 0.  Writes the dealiased

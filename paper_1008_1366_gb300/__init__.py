@@ -18,5 +18,6 @@ from .api import (  # noqa: F401
     conv_ternary_hermitian_1d,
     prepare,
     read_status,
+    read_trace,
     workspace_size,
 )

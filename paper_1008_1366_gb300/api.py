@@ -85,6 +85,16 @@ def read_status(work):
     return st.value, det.value
 
 
+def read_trace(work):
+    """Trace counters of the last fixed-engine launch on `work`
+    (dc_read_trace): waits, and SM cycles / task counts per task type."""
+    out = (ctypes.c_uint64 * 10)()
+    check(_native.lib().dc_read_trace(_vp(work), _stream(work), out), "dc_read_trace")
+    names = ("L1", "A", "B", "C")
+    return {"waited": out[0], "wait_cycles": out[1],
+            "cycles": dict(zip(names, out[2:6])), "tasks": dict(zip(names, out[6:10]))}
+
+
 def _run_1d(name, kind, ins, nout, out):
     dt = _inputs(*ins)
     if ins[0].dim() != 1:
@@ -224,6 +234,9 @@ class BatchedPlan:
         self._work = None
 
     def workspace(self, device):
+        device = torch.device(device)
+        if device.type == "cuda" and device.index is None:
+            device = torch.device("cuda", torch.cuda.current_device())
         if self._work is None or self._work.device != device or self._work.numel() < self.workspace_bytes:
             self._work = _work(self.workspace_bytes, device)
         return self._work

@@ -205,6 +205,20 @@ dc_status dc_read_status(const void* work, void* stream, int32_t* status, int32_
   return DC_OK;
 }
 
+dc_status dc_read_trace(const void* work, void* stream, uint64_t* out) {
+  if (!work || !out) return DC_ERR_ARG;
+  WorkHeader h;
+  DC_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  DC_CUDA_TRY(cudaMemcpy(&h, work, sizeof(h), cudaMemcpyDeviceToHost));
+  out[0] = h.waited;
+  out[1] = h.wait_cycles;
+  for (int k = 0; k < 4; ++k) {
+    out[2 + k] = h.type_cycles[k];
+    out[6 + k] = h.type_count[k];
+  }
+  return DC_OK;
+}
+
 dc_status dc_conv_complex_1d(const void* f, const void* g, void* h, int64_t m, int32_t dtype,
                              void* work, size_t work_bytes, void* stream) {
   const void* ins[2] = {f, g};

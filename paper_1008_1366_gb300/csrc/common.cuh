@@ -42,7 +42,9 @@ struct WorkHeader {
   uint32_t counter;   // persistent-queue counter, reset before each launch
   uint32_t waited;    // task-queue kernels: tasks that found a dependency unmet
   unsigned long long wait_cycles;   // and the SM cycles they spent waiting
-  uint32_t pad[58];
+  unsigned long long type_cycles[4];   // SM cycles spent in tasks of each type
+  uint32_t type_count[4];              // and the number of such tasks
+  uint32_t pad[46];
 };
 static_assert(sizeof(WorkHeader) == 256, "workspace header is 256 bytes");
 

@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
       cur = code;
       __syncthreads();
     }
+    const long long t_start = clock64();
     switch (code) {
 #define DC_FX_CASE(c) \
       case c: run_size<size_of_code(c)>(&a, type, t.a, t.b, sm, rt); break;
@@ -357,9 +358,13 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
       default: break;
     }
     __syncthreads();
-    if (threadIdx.x == 0 && t.sidx >= 0) {
-      __threadfence();
-      atomicAdd(a.cnt + t.sidx, 1u);
+    if (threadIdx.x == 0) {
+      // the barrier above orders every thread's stores of the task before
+      // this release at GPU scope
+      if (t.sidx >= 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.cnt + t.sidx) : "memory");
+      // per-type time, for tracing where a launch spends its cycles
+      atomicAdd(&a.hdr->type_cycles[type & 3], (unsigned long long)(clock64() - t_start));
+      atomicAdd(&a.hdr->type_count[type & 3], 1u);
     }
   }
 }
@@ -443,7 +448,13 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
       l1t.push_back(std::move(t));
     }
   }
-  std::stable_sort(l1t.begin(), l1t.end(), [](const L1T& x, const L1T& y) { return x.cost > y.cost; });
+  // largest sizes first and each size's tasks together: blocks that run at
+  // the same time then run the same code (one size's code is tens of KB of
+  // straight-line instructions) and refill their root tables less often
+  std::stable_sort(l1t.begin(), l1t.end(), [](const L1T& x, const L1T& y) {
+    return size_of_code(x.code) != size_of_code(y.code) ? size_of_code(x.code) > size_of_code(y.code)
+                                                        : x.cost > y.cost;
+  });
   std::vector<Task> l1tasks;
   for (auto& t : l1t) {
     Task k{(T_L1 << 8) | t.code, (int32_t)P.order.size(), (int32_t)t.ids.size(), -1, 0, -1};

@@ -84,6 +84,16 @@ def test_partial_groups_and_order(dc, dtype):
     check_all(sizes, f, g, off, h, dtype)
 
 
+def test_trace_counts_every_task(dc):
+    # the header's trace counts one entry per task of the queue
+    sizes = [65536] * 2 + [640] * 20 + [64] * 130
+    plan, f, g, off, h = run_plan(dc, sizes, 29)
+    tr = dc.read_trace(plan.workspace(torch.device("cuda")))
+    # 65536 = 256 x 256: 16 column tiles (A and C) and 32 row groups (B) each
+    assert tr["tasks"] == {"L1": 3 + 3, "A": 32, "B": 64, "C": 32}, tr
+    assert all(v > 0 for v in tr["cycles"].values())
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_level2_region_reuse(dc, dtype):
     # many level-2 instances: more batches than the four scratch regions
