@@ -397,23 +397,32 @@ def main():
     value = convs_total / (t_ms / 1e3)
     ms_step = t_ms / args.steps
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers: the
+    # host-to-host call (dc_conv_complex_1d_batched_host) copies chunks of
+    # instances in, convolves and copies out on overlapping streams; every
+    # step copies all inputs in and all results out.  The chunk count is the
+    # best of a few, each timed on its own.
     hf = torch.tensor(f, dtype=torch.complex64).pin_memory()
     hg = torch.tensor(g, dtype=torch.complex64).pin_memory()
     hout = torch.empty_like(hf).pin_memory()
     e2e_steps = max(3, min(args.steps, 10))
-    with torch.cuda.stream(stream):
-        for k in range(2 + e2e_steps):
-            if k == 2:
-                stream.synchronize()
-                t0 = time.perf_counter()
-            tf.copy_(hf, non_blocking=True)
-            tg.copy_(hg, non_blocking=True)
-            plan(tf, tg, out=th, work=work)
-            hout.copy_(th, non_blocking=True)
-        stream.synchronize()
-        e2e_s = time.perf_counter() - t0
-    e2e_val = n_inst * world * e2e_steps / e2e_s
+    e2e_best = None
+    for nchunks in (1, 8, 16, 32):
+        hw = plan.host_workspace(nchunks, dev)
+        with torch.cuda.stream(stream):
+            for k in range(2 + e2e_steps):
+                if k == 2:
+                    stream.synchronize()
+                    t0 = time.perf_counter()
+                plan.run_from_host(hf, hg, hout, tf, tg, th, hw, nchunks)
+            stream.synchronize()
+            e2e_s = time.perf_counter() - t0
+        val = n_inst * world * e2e_steps / e2e_s
+        if e2e_best is None or val > e2e_best[0]:
+            e2e_best = (val, nchunks)
+        del hw
+    e2e_val, e2e_chunks = e2e_best
+    e2e_ok = bool(np.allclose(hout.numpy(), hh, rtol=0, atol=0))
 
     # plain FP64 path: one launch per instance
     fp64 = None
@@ -486,7 +495,8 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "convs/s", "h2d_bytes_per_step": 2 * total * 8,
-                    "d2h_bytes_per_step": total * 8},
+                    "d2h_bytes_per_step": total * 8, "chunks": e2e_chunks,
+                    "api": "dc_conv_complex_1d_batched_host", "result_equals_device_path": e2e_ok},
             "clocks": clk.summary(),
             "gpu_launches": args.steps * plan.launches,
             "parity": {"max_rel_l2_sampled": worst, "worst_err_over_tol": worst_ratio,

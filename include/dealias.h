@@ -244,6 +244,24 @@ dc_status dc_conv_complex_1d_batched(const dc_batched_plan* plan, const void* f,
  * device memory), readable with dc_read_status after the stream completes.
  * Nothing faults or hangs.  DC_ERR_ARG / ALIGN / NOMEM on bad arguments. */
 dc_status dc_selftest_wait_timeout(void* work, size_t work_bytes, int64_t cycles, void* stream);
+/* End-to-end batched convolution from host memory (no counterpart in the
+ * paper: a transfer schedule).  The instances are split into `nchunks`
+ * chunks of consecutive instances with about equal element counts; chunk k's
+ * slices of hf, hg are copied into df, dg, its convolutions run as soon as
+ * they have arrived, and its results are copied from dh back to hh, each
+ * step on library streams, so that copies in both directions overlap
+ * the computation of other chunks.  The streams start after the work
+ * already enqueued on `stream`, and `stream` continues after all of it.
+ * hf, hg, hh: host arrays of the packed layout (page-locked for the copies
+ * to overlap); df, dg, dh: device arrays of the same size; work: device
+ * workspace of dc_batched_plan_host_workspace_size bytes for this nchunks.
+ * The first call for a given nchunks plans the chunks (device allocation;
+ * call dc_batched_plan_host_workspace_size first to keep it out of a
+ * captured graph).  Results equal dc_conv_complex_1d_batched's. */
+dc_status dc_batched_plan_host_workspace_size(dc_batched_plan* plan, int32_t nchunks, size_t* bytes);
+dc_status dc_conv_complex_1d_batched_host(dc_batched_plan* plan, const void* hf, const void* hg, void* hh,
+                                          void* df, void* dg, void* dh, void* work, size_t work_bytes,
+                                          int32_t nchunks, void* stream);
 dc_status dc_batched_plan_destroy(dc_batched_plan* plan);
 
 #ifdef __cplusplus

@@ -44,6 +44,8 @@ SIGNATURES = {
     "dc_batched_plan_set_schedule": [_vp, _i32, _i32],
     "dc_selftest_wait_timeout": [_vp, _sz, _i64, _vp],
     "dc_read_trace": [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)],
+    "dc_batched_plan_host_workspace_size": [_vp, _i32, ctypes.POINTER(_sz)],
+    "dc_conv_complex_1d_batched_host": [_vp] + [_vp] * 7 + [_sz, _i32, _vp],
     "dc_conv_complex_1d_batched": [_vp, _vp, _vp, _vp, _vp, _sz, _vp],
     "dc_batched_plan_destroy": [_vp],
 }

@@ -252,6 +252,28 @@ class BatchedPlan:
               "dc_conv_complex_1d_batched")
         return out
 
+    def host_workspace(self, nchunks, device):
+        """Device workspace for run_from_host with this many chunks."""
+        ws = ctypes.c_size_t(0)
+        check(_native.lib().dc_batched_plan_host_workspace_size(self.handle, int(nchunks), ctypes.byref(ws)),
+              "dc_batched_plan_host_workspace_size")
+        return _work(ws.value, device)
+
+    def run_from_host(self, hf, hg, hh, df, dg, dh, work, nchunks):
+        """Host-to-host pipelined execution (dc_conv_complex_1d_batched_host):
+        hf, hg, hh are CPU tensors (pinned), df, dg, dh CUDA tensors of the same
+        packed layout; runs on the current stream."""
+        for t in (hf, hg, hh):
+            if t.is_cuda or t.dtype != self.dtype or t.numel() != self.total or not t.is_contiguous():
+                raise ValueError("host arrays must be contiguous CPU tensors of the plan's size and dtype")
+        for t in (df, dg, dh):
+            if not t.is_cuda or t.dtype != self.dtype or t.numel() != self.total or not t.is_contiguous():
+                raise ValueError("device arrays must be contiguous CUDA tensors of the plan's size and dtype")
+        check(_native.lib().dc_conv_complex_1d_batched_host(
+            self.handle, _vp(hf), _vp(hg), _vp(hh), _vp(df), _vp(dg), _vp(dh), _vp(work), work.numel(),
+            int(nchunks), _stream(df)), "dc_conv_complex_1d_batched_host")
+        return hh
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:

@@ -53,6 +53,16 @@ struct dc_batched_plan {
   std::vector<int64_t> off_host;
   // plain mode: one launch per instance over its own task range
   std::vector<int32_t> inst_first, inst_count;
+  // pipelined host-to-host execution: chunk plans over consecutive instances
+  struct Chunks {
+    int n = 0;
+    std::vector<dc_batched_plan*> plans;
+    std::vector<int32_t> first;      // first instance of each chunk
+    size_t work = 0;                 // shared workspace of the chunk plans
+    cudaStream_t st[4] = {nullptr, nullptr, nullptr, nullptr};   // copy f in, compute, copy out, copy g in
+    std::vector<cudaEvent_t> ev;     // per chunk: f arrived, results ready, g arrived; then 5 joins
+  } chunks;
+  std::vector<int64_t> m_host;
 };
 
 // one precision of the fixed-shape engine
@@ -340,6 +350,50 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
   }
   return DC_OK;
 }
+void free_chunks(dc_batched_plan* p) {
+  auto& c = p->chunks;
+  for (auto* q : c.plans) dc_batched_plan_destroy(q);
+  for (auto e : c.ev) cudaEventDestroy(e);
+  for (auto& s : c.st)
+    if (s) cudaStreamDestroy(s);
+  c = dc_batched_plan::Chunks{};
+}
+
+// Splits the instances into n chunks of consecutive instances with about
+// equal element counts and plans each (same dtype and flags, never the
+// one-per-launch mode); streams and events for the pipelined execution.
+dc_status make_chunks(dc_batched_plan* p, int n) {
+  if (p->chunks.n == n) return DC_OK;
+  free_chunks(p);
+  auto& c = p->chunks;
+  n = std::max(1, std::min(n, p->n));
+  const int flags = p->flags & ~DC_PLAN_ONE_PER_LAUNCH;
+  int32_t i = 0;
+  for (int k = 0; k < n && i < p->n; ++k) {
+    const int64_t goal = p->total * (k + 1) / n;
+    int32_t j = i + 1;
+    while (j < p->n && (p->off_host[j] < goal || k == n - 1)) ++j;
+    dc_batched_plan* q = nullptr;
+    dc_status st = dc_batched_plan_create(p->m_host.data() + i, j - i, p->dtype, flags, &q);
+    if (st != DC_OK) { free_chunks(p); return st; }
+    c.plans.push_back(q);
+    c.first.push_back(i);
+    c.work = std::max(c.work, q->work);
+    i = j;
+  }
+  c.first.push_back(p->n);
+  for (auto& s : c.st) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { dc_set_last_cuda_error(e); free_chunks(p); return DC_ERR_CUDA; }
+  }
+  c.ev.resize(3 * c.plans.size() + 5);
+  for (auto& e : c.ev) {
+    cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (r != cudaSuccess) { dc_set_last_cuda_error(r); free_chunks(p); return DC_ERR_CUDA; }
+  }
+  c.n = n;
+  return DC_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -363,6 +417,8 @@ dc_status dc_batched_plan_create(const int64_t* m, int32_t n, int32_t dtype, int
     by_size[m[i]].push_back(i);
   }
   p->total = off[n];
+  p->m_host.assign(m, m + n);
+  p->off_host = off;
 
   bool all_fixed = true;
   for (int32_t i = 0; i < n && all_fixed; ++i) all_fixed = fx::f32::size_code(m[i]) >= 0;
@@ -568,8 +624,72 @@ dc_status dc_conv_complex_1d_batched(const dc_batched_plan* p, const void* f, co
   return launch_conv1d(K_COMPLEX, p->ds, a, p->grid, p->smem, s);
 }
 
+dc_status dc_batched_plan_host_workspace_size(dc_batched_plan* p, int32_t nchunks, size_t* bytes) {
+  if (!p || !bytes || nchunks < 1) return DC_ERR_ARG;
+  dc_status st = make_chunks(p, nchunks);
+  if (st != DC_OK) return st;
+  *bytes = p->chunks.work;
+  return DC_OK;
+}
+
+dc_status dc_conv_complex_1d_batched_host(dc_batched_plan* p, const void* hf, const void* hg, void* hh,
+                                          void* df, void* dg, void* dh, void* work, size_t work_bytes,
+                                          int32_t nchunks, void* stream) {
+  if (!p || !hf || !hg || !hh || !df || !dg || !dh || !work || nchunks < 1) return DC_ERR_ARG;
+  const size_t a8 = (size_t)p->ds;
+  if ((uintptr_t)df % a8 || (uintptr_t)dg % a8 || (uintptr_t)dh % a8 || (uintptr_t)work % 256)
+    return DC_ERR_ALIGN;
+  dc_status st = make_chunks(p, nchunks);
+  if (st != DC_OK) return st;
+  auto& c = p->chunks;
+  if (work_bytes < c.work) return DC_ERR_NOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nc = (int)c.plans.size();
+  cudaEvent_t* evf = &c.ev[0];
+  cudaEvent_t* evh = &c.ev[nc];
+  cudaEvent_t* evg = &c.ev[2 * nc];
+  cudaEvent_t start = c.ev[3 * nc], j0 = c.ev[3 * nc + 1], j1 = c.ev[3 * nc + 2], j2 = c.ev[3 * nc + 3],
+              j3 = c.ev[3 * nc + 4];
+  // the four streams start after the work already on `stream`
+  DC_CUDA_TRY(cudaEventRecord(start, s));
+  for (auto& q : c.st) DC_CUDA_TRY(cudaStreamWaitEvent(q, start, 0));
+  auto bytes_of = [&](int k) { return (size_t)(p->off_host[c.first[k + 1]] - p->off_host[c.first[k]]) * a8; };
+  auto at = [&](const void* base, int k) { return (const char*)base + (size_t)p->off_host[c.first[k]] * a8; };
+  // f and g come in on one stream (a second one measured no faster: the
+  // host link is the limit), h goes out on another
+  for (int k = 0; k < nc; ++k) {
+    DC_CUDA_TRY(cudaMemcpyAsync((void*)at(df, k), at(hf, k), bytes_of(k), cudaMemcpyHostToDevice, c.st[0]));
+    DC_CUDA_TRY(cudaEventRecord(evf[k], c.st[0]));
+    DC_CUDA_TRY(cudaMemcpyAsync((void*)at(dg, k), at(hg, k), bytes_of(k), cudaMemcpyHostToDevice, c.st[0]));
+    DC_CUDA_TRY(cudaEventRecord(evg[k], c.st[0]));
+  }
+  for (int k = 0; k < nc; ++k) {
+    DC_CUDA_TRY(cudaStreamWaitEvent(c.st[1], evf[k], 0));
+    DC_CUDA_TRY(cudaStreamWaitEvent(c.st[1], evg[k], 0));
+    st = dc_conv_complex_1d_batched(c.plans[k], at(df, k), at(dg, k), (void*)at(dh, k), work, work_bytes,
+                                    c.st[1]);
+    if (st != DC_OK) return st;
+    DC_CUDA_TRY(cudaEventRecord(evh[k], c.st[1]));
+  }
+  for (int k = 0; k < nc; ++k) {
+    DC_CUDA_TRY(cudaStreamWaitEvent(c.st[2], evh[k], 0));
+    DC_CUDA_TRY(cudaMemcpyAsync((void*)at(hh, k), at(dh, k), bytes_of(k), cudaMemcpyDeviceToHost, c.st[2]));
+  }
+  // `stream` continues after all four
+  DC_CUDA_TRY(cudaEventRecord(j0, c.st[0]));
+  DC_CUDA_TRY(cudaEventRecord(j1, c.st[1]));
+  DC_CUDA_TRY(cudaEventRecord(j2, c.st[2]));
+  DC_CUDA_TRY(cudaEventRecord(j3, c.st[3]));
+  DC_CUDA_TRY(cudaStreamWaitEvent(s, j0, 0));
+  DC_CUDA_TRY(cudaStreamWaitEvent(s, j1, 0));
+  DC_CUDA_TRY(cudaStreamWaitEvent(s, j2, 0));
+  DC_CUDA_TRY(cudaStreamWaitEvent(s, j3, 0));
+  return DC_OK;
+}
+
 dc_status dc_batched_plan_destroy(dc_batched_plan* p) {
   if (!p) return DC_ERR_ARG;
+  free_chunks(p);
   if (p->dmem) cudaFree(p->dmem);
   delete p;
   return DC_OK;

@@ -197,3 +197,39 @@ def test_bounded_wait_reports_timeout(dc):
     assert L.dc_selftest_wait_timeout(ctypes.c_void_p(work.data_ptr()), 100, 1000, s) == 6
     assert L.dc_selftest_wait_timeout(ctypes.c_void_p(work.data_ptr() + 8), 4000, 1000, s) == 3
     assert L.dc_selftest_wait_timeout(ctypes.c_void_p(0), 4096, 1000, s) == 1
+
+
+@pytest.mark.parametrize("nchunks", [1, 3, 8])
+def test_host_pipeline_matches(dc, nchunks):
+    # host-to-host pipelined execution gives the device path's bits
+    sizes = list(synthetic.batched_sizes(200, 31))
+    f, g, off = synthetic.batched_inputs(sizes, 30)
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex64)
+    df = torch.tensor(f, dtype=torch.complex64, device="cuda")
+    dg = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    ref = plan(df, dg).cpu()
+    hf = torch.tensor(f, dtype=torch.complex64).pin_memory()
+    hg = torch.tensor(g, dtype=torch.complex64).pin_memory()
+    hh = torch.zeros_like(hf).pin_memory()
+    dh = torch.empty_like(df)
+    df.zero_()
+    dg.zero_()
+    work = plan.host_workspace(nchunks, df.device)
+    plan.run_from_host(hf, hg, hh, df, dg, dh, work, nchunks)
+    torch.cuda.synchronize()
+    assert torch.equal(hh, ref)
+
+
+def test_host_pipeline_runtime_engine(dc):
+    # also for plans on the runtime-shaped engine (a size outside the set)
+    sizes = [48, 1024, 7 * 0 + 6, 3072, 96]
+    f, g, off = synthetic.batched_inputs(sizes, 32)
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex128)
+    hf = torch.tensor(f, dtype=torch.complex128).pin_memory()
+    hg = torch.tensor(g, dtype=torch.complex128).pin_memory()
+    hh = torch.zeros_like(hf).pin_memory()
+    df, dg, dh = (torch.empty(hf.numel(), dtype=torch.complex128, device="cuda") for _ in range(3))
+    work = plan.host_workspace(2, df.device)
+    plan.run_from_host(hf, hg, hh, df, dg, dh, work, 2)
+    torch.cuda.synchronize()
+    check_all(sizes, f, g, off, hh.numpy(), torch.complex128)
