@@ -39,6 +39,14 @@ __device__ __forceinline__ void discard_l2(const void* p) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
+// asynchronous 16-byte global-to-shared copies (L2 only), their commit and wait
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // size codes: 2^6..2^16, 3*2^5..3*2^14, 5*2^4..5*2^13
 __host__ __device__ constexpr int size_of_code(int c) {
   return c < 11 ? (64 << c) : (c < 21 ? (96 << (c - 11)) : (80 << (c - 21)));
@@ -81,9 +89,11 @@ template <int M> struct Shape {
   static_assert(l1 || (L1 % W == 0 && (2 * L2) % GR == 0 && L1 * L2 == M), "level-2 tiling must be exact");
   static_assert(!l1 || kThreads % T == 0, "level-1 groups must tile the block");
   static constexpr int CB = (int)sizeof(C);
+  // level 2: the row groups of pass B, or two column tiles (the transform
+  // buffer and the prefetched g tile of pass A)
   static constexpr int smem = l1 ? G * group_stride(M, T) * CB
-                                 : (GR * group_stride(L1, T1) * CB > W * L2 * CB ? GR * group_stride(L1, T1) * CB
-                                                                                   : W * L2 * CB);
+                                 : (GR * group_stride(L1, T1) * CB > 2 * W * L2 * CB ? GR * group_stride(L1, T1) * CB
+                                                                                       : 2 * W * L2 * CB);
   // FP32: two blocks per SM, FP64: one (228 KB per SM less 1 KB reserved per
   // block and the static shared variables)
   static_assert(smem + kRootsMax * CB <= (233472 - kBlocksPerSM * 1024) / kBlocksPerSM - 64,
@@ -171,14 +181,37 @@ __device__ __noinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, Root
   for (int b = 0; b < K::NB; ++b)
 #pragma unroll
     for (int q = 0; q < K::R; ++q) tw[b * K::R + q] = rt.at(k1 + L1 * pos<L2, E, 0, false>(i, b, q));
+  // g's column tile comes into shared memory, behind the transform buffer,
+  // while f's columns are transformed (16-byte copies; instance offsets and
+  // tile starts are multiples of 16 elements)
+  C* gt = sm + W * L2;
+  {
+    constexpr int CPR = W * (int)sizeof(C) / 16;   // 16-byte chunks per tile row
+    const char* gsrc = (const char*)((const C*)a->g + in.off + (size_t)tile * W);
+    for (int ch = threadIdx.x; ch < L2 * CPR; ch += kThreads) {
+      const int row = ch / CPR, col = ch % CPR;
+      cp_async16((char*)gt + ((size_t)row * W * sizeof(C) + (size_t)col * 16),
+                 gsrc + ((size_t)row * L1 * sizeof(C) + (size_t)col * 16));
+    }
+    cp_async_commit();
+  }
 #pragma unroll 1
   for (int arr = 0; arr < 2; ++arr) {
-    const C* x = (const C*)(arr ? a->g : a->f) + in.off + k1;
     C raw[E];
+    if (arr == 0) {
+      const C* x = (const C*)a->f + in.off + k1;
 #pragma unroll
-    for (int b = 0; b < K::NB; ++b)
+      for (int b = 0; b < K::NB; ++b)
 #pragma unroll
-      for (int q = 0; q < K::R; ++q) raw[b * K::R + q] = __ldg(x + L1 * pos<L2, E, 0, false>(i, b, q));
+        for (int q = 0; q < K::R; ++q) raw[b * K::R + q] = __ldg(x + L1 * pos<L2, E, 0, false>(i, b, q));
+    } else {
+      cp_async_wait_all();
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+        for (int q = 0; q < K::R; ++q) raw[b * K::R + q] = gt[pos<L2, E, 0, false>(i, b, q) * W + c];
+    }
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
       C v[E];
