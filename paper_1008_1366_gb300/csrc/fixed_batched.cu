@@ -242,22 +242,15 @@ __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Root
   // inputs times zeta_m^{j2 k1} (one lookup for f, g and the output, whose
   // register e sits at the same position), output times zeta_m^{-j2 k1}
   const GroupSync<T1> sync{1 + gi};
-  if constexpr (E1 <= 20) {
-    C tw[E1];
-    conv_residue<L1, E1, TN>(
-        i, true, A, B, rt,
-        [&](int x, int arr, int e) {
-          if (arr == 0) tw[e] = rt.at(2 * j2 * x);
-          return cmul(__ldcg((arr ? sg : (const C*)sf) + x), tw[e]);
-        },
-        [&](int x, int e, C v) { __stcg(sf + x, cmulc(v, tw[e])); }, sync);
-  } else {
-    // E1 = 24: one lookup per use is cheaper than 24 more live registers
-    conv_residue<L1, E1, TN>(
-        i, true, A, B, rt,
-        [&](int x, int arr, int) { return cmul(__ldcg((arr ? sg : (const C*)sf) + x), rt.at(2 * j2 * x)); },
-        [&](int x, int, C v) { __stcg(sf + x, cmulc(v, rt.at(2 * j2 * x))); }, sync);
-  }
+  static_assert(E1 <= 20, "rows hold their twiddles in registers");
+  C tw[E1];
+  conv_residue<L1, E1, TN>(
+      i, true, A, B, rt,
+      [&](int x, int arr, int e) {
+        if (arr == 0) tw[e] = rt.at(2 * j2 * x);
+        return cmul(__ldcg((arr ? sg : (const C*)sf) + x), tw[e]);
+      },
+      [&](int x, int e, C v) { __stcg(sf + x, cmulc(v, tw[e])); }, sync);
   // the g row was read for the last time (every thread of the group loaded
   // its part before the group's first barrier)
   for (int ln = i; ln < L1 * (int)sizeof(C) / 128; ln += T1) discard_l2((const char*)sg + ln * 128);
