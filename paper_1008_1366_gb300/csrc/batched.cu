@@ -47,6 +47,7 @@ struct dc_batched_plan {
   fx::HostPlan hp;
   fx::Task* d_tasks = nullptr;
   fx::L2Inst* d_l2 = nullptr;
+  int64_t* d_l1tmp = nullptr;
   const void* tabs[fx::kNumSizes] = {};
   size_t cnt_bytes = 0;   // header + counters, zeroed before each launch
   fx::Schedule fx_sched{0, 0};   // queue order of the fixed engine
@@ -171,8 +172,12 @@ dc_status autotune_size(int64_t m, int count, int ds, int smem_max, CfgDev* best
   cudaGetLastError();
   return DC_OK;
 }
+// workspace: header + counters | level-2 scratch | level-1 partial outputs
+size_t fx_tmp_offset(const dc_batched_plan* p) {
+  return p->cnt_bytes + align_up(p->hp.scratch * (size_t)p->ds, 256);
+}
 size_t fx_work_bytes(const dc_batched_plan* p) {
-  return p->cnt_bytes + p->hp.scratch * (size_t)p->ds;
+  return fx_tmp_offset(p) + p->hp.l1_elems * (size_t)p->ds;
 }
 
 dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
@@ -182,11 +187,15 @@ dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
   const size_t bl = align_up(std::max<size_t>(1, hp.l2.size()) * sizeof(fx::L2Inst), 256);
   const size_t bo = align_up(std::max<size_t>(1, hp.order.size()) * sizeof(int32_t), 256);
   const size_t bf = align_up(off.size() * sizeof(int64_t), 256);
-  DC_CUDA_TRY(cudaMalloc(&p->dmem, bt + bl + bo + bf));
+  const size_t bp = align_up(std::max<size_t>(1, hp.l1tmp.size()) * sizeof(int64_t), 256);
+  DC_CUDA_TRY(cudaMalloc(&p->dmem, bt + bl + bo + bf + bp));
   p->d_tasks = (fx::Task*)p->dmem;
   p->d_l2 = (fx::L2Inst*)(p->dmem + bt);
   p->d_order = (int32_t*)(p->dmem + bt + bl);
   p->d_off = (int64_t*)(p->dmem + bt + bl + bo);
+  p->d_l1tmp = (int64_t*)(p->dmem + bt + bl + bo + bf);
+  if (!hp.l1tmp.empty())
+    DC_CUDA_TRY(cudaMemcpy(p->d_l1tmp, hp.l1tmp.data(), hp.l1tmp.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   if (!hp.tasks.empty())
     DC_CUDA_TRY(cudaMemcpy(p->d_tasks, hp.tasks.data(), hp.tasks.size() * sizeof(fx::Task), cudaMemcpyHostToDevice));
   if (!hp.l2.empty())
@@ -212,6 +221,8 @@ fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void*
   a.hdr = (WorkHeader*)work;
   a.cnt = (uint32_t*)((char*)work + sizeof(WorkHeader));
   a.scratch = (char*)work + p->cnt_bytes;
+  a.tmp = (char*)work + fx_tmp_offset(p);
+  a.l1tmp = p->d_l1tmp;
   a.wait_limit = fx::kWaitLimit;
   for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
   return a;
@@ -290,6 +301,8 @@ bool fx_build_plain(dc_batched_plan* p, const int64_t* m, int32_t n, const std::
     all.l2.insert(all.l2.end(), one.l2.begin(), one.l2.end());
     all.ncnt += one.ncnt;
     all.scratch = std::max(all.scratch, one.scratch);
+    all.l1tmp.push_back(0);   // the launches run one after another: one shared region
+    all.l1_elems = std::max(all.l1_elems, one.l1_elems);
     all.smem = std::max(all.smem, one.smem);
     for (int c : one.codes)
       if (std::find(all.codes.begin(), all.codes.end(), c) == all.codes.end()) all.codes.push_back(c);
@@ -696,3 +709,61 @@ dc_status dc_batched_plan_destroy(dc_batched_plan* p) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Uniform batches on the fixed-shape engine: n instances of size m at stride
+// m (the single 1D complex call, the row convolutions of the multi-D complex
+// paths).  Plans are created on first use per (device, n, m, precision) and
+// kept until exit, like the root tables.
+// ---------------------------------------------------------------------------
+#include <mutex>
+#include <tuple>
+
+namespace dc {
+namespace {
+std::mutex g_umu;
+std::map<std::tuple<int, int64_t, int64_t, int>, dc_batched_plan*> g_uplans;
+}  // namespace
+
+bool fx_uniform_ok(int64_t m, int ds) { return (ds == 8 || ds == 16) && fx::f32::size_code(m) >= 0; }
+
+bool fx_uniform_two_level(int64_t m) {
+  const int c = fx::f32::size_code(m);
+  if (c < 0) return false;
+  int lv, per, l1, l2, w;
+  fx::f32::code_shape(c, &lv, &per, &l1, &l2, &w);   // the same split in both precisions
+  return lv == 2;
+}
+
+size_t fx_uniform_work(int64_t n, int64_t m, int ds) {
+  const FxOps* ops = ds == 8 ? &kFx32 : &kFx64;
+  int smem_all = 0;
+  for (int c = 0; c < fx::kNumSizes; ++c) smem_all = std::max(smem_all, ops->code_smem(c));
+  const int bps = ds == 8 ? 2 : 1;   // the kernel's blocks per SM (launch bounds)
+  std::vector<int64_t> ms((size_t)n, m), off((size_t)n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) off[i + 1] = off[i] + m;
+  fx::HostPlan hp;
+  const fx::Schedule sc{bps * device_info().sms / 2, 0};
+  if (!ops->build_plan(ms.data(), (int32_t)n, off.data(), sc, &hp)) return 0;
+  (void)smem_all;
+  return align_up(sizeof(WorkHeader) + hp.ncnt * sizeof(uint32_t), 256) + align_up(hp.scratch * (size_t)ds, 256) +
+         hp.l1_elems * (size_t)ds;
+}
+
+dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, dc_batched_plan** out) {
+  int dev = 0;
+  DC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_umu);
+  auto key = std::make_tuple(dev, n, m, ds);
+  auto it = g_uplans.find(key);
+  if (it != g_uplans.end()) { *out = it->second; return DC_OK; }
+  std::vector<int64_t> ms((size_t)n, m);
+  dc_batched_plan* p = nullptr;
+  dc_status st = dc_batched_plan_create(ms.data(), (int32_t)n, ds == 8 ? DC_C64 : DC_C128, 0, &p);
+  if (st != DC_OK) return st;
+  g_uplans[key] = p;
+  *out = p;
+  return DC_OK;
+}
+
+}  // namespace dc

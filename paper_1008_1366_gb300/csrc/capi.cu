@@ -100,6 +100,17 @@ dc_status plan_1d(int kind, int64_t m, int ds, bool with_table, CfgDev* cfg, siz
     cfg->tw = tw;
   }
   *work = kHeader + align_up(cfg_scratch_bytes(kind, *cfg, ds), 256);
+  // a single binary complex convolution of a two-level size runs on the
+  // fixed-shape engine (a one-instance plan, cached): its passes spread over
+  // many blocks, where the runtime-shaped kernel gives the instance one
+  if (kind == K_COMPLEX && fx_uniform_ok(m, ds) && fx_uniform_two_level(m)) {
+    *work = std::max(*work, fx_uniform_work(1, m, ds));
+    if (with_table) {
+      dc_batched_plan* p = nullptr;
+      dc_status st = fx_uniform_plan(1, m, ds, &p);
+      if (st != DC_OK) return st;
+    }
+  }
   return DC_OK;
 }
 
@@ -115,6 +126,11 @@ dc_status run_1d(int kind, const void* const* ins, int nin, void* const* outs, i
   if (st != DC_OK) return st;
   if ((st = check_work(work, work_bytes, need)) != DC_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  if (kind == K_COMPLEX && fx_uniform_ok(m, ds) && fx_uniform_two_level(m)) {
+    dc_batched_plan* p = nullptr;
+    if ((st = fx_uniform_plan(1, m, ds, &p)) != DC_OK) return st;
+    return dc_conv_complex_1d_batched(p, ins[0], ins[1], outs[0], work, work_bytes, s);
+  }
   ConvArgs a{};
   for (int x = 0; x < nin; ++x) a.in[x] = ins[x];
   for (int o = 0; o < nout; ++o) a.out[o] = outs[o];

@@ -49,6 +49,8 @@ struct FxArgs {
   uint32_t* cnt;           // dependency counters, zero before each launch
   WorkHeader* hdr;         // status word and queue counter, zero before each launch
   void* scratch;
+  void* tmp;               // level-1 partial outputs (residue 0), tmp + l1tmp[instance]
+  const int64_t* l1tmp;
   long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
   const void* tab[kNumSizes];     // root tables zeta_{2m}^i, i < 2m, per size code
 };
@@ -59,6 +61,8 @@ struct HostPlan {
   std::vector<int32_t> order;
   size_t ncnt = 0;          // dependency counters
   size_t scratch = 0;       // scratch elements
+  std::vector<int64_t> l1tmp;   // per instance: element offset of its level-1 partial output
+  size_t l1_elems = 0;          // elements of the partial-output region
   int smem = 0;             // dynamic shared memory of the launch
   std::vector<int> codes;   // distinct size codes of the plan
 };

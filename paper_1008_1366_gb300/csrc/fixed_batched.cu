@@ -117,6 +117,9 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
   const C* f = (const C*)a->f + off;
   const C* g = (const C*)a->g + off;
   C* h = (C*)a->h + off;
+  // residue 0's partial output goes to a region of the workspace, so h is
+  // written once, at residue 1, after every read of f and g (in-place calls)
+  C* hp = (C*)a->tmp + (act ? a->l1tmp[a->order[first + gi]] : 0);
   C* A = sm + gi * GS;
   C* B = A + PL;
   const Real sc = (Real)1 / (Real)(2 * M);
@@ -131,7 +134,7 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
     conv_residue<M, E, TN>(
         i, true, A, B, rt, [&](int x, int arr, int) { return act ? __ldg((arr ? g : f) + x) : zero; },
         [&](int x, int, C v) {
-          if (act) h[x] = cscale(v, sc);
+          if (act) hp[x] = cscale(v, sc);
         },
         sync);
   } else {
@@ -148,7 +151,7 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
       conv_residue<M, E, TN>(
           i, true, A, B, rt, ld,
           [&](int x, int e, C v) {
-            if (act) h[x] = cadd(h[x], cscale(cmulc(v, tw[e]), sc));
+            if (act) h[x] = cadd(hp[x], cscale(cmulc(v, tw[e]), sc));
           },
           sync);
     } else {
@@ -157,7 +160,7 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
       conv_residue<M, E, TN>(
           i, true, A, B, rt, ld,
           [&](int x, int, C v) {
-            if (act) h[x] = cadd(h[x], cscale(cmulc(v, rt.at(x)), sc));
+            if (act) h[x] = cadd(hp[x], cscale(cmulc(v, rt.at(x)), sc));
           },
           sync);
     }
@@ -447,12 +450,18 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   std::map<int, std::vector<int32_t>> l1_by_code;
   std::vector<std::pair<int, int32_t>> big;   // (code, instance)
   std::vector<bool> used(kNumSizes, false);
+  P.l1tmp.assign((size_t)n, 0);
   for (int32_t i = 0; i < n; ++i) {
     const int c = size_code(m[i]);
     if (c < 0) return false;
     used[c] = true;
-    if (tb.lvl[c] == 1) l1_by_code[c].push_back(i);
-    else big.push_back({c, i});
+    if (tb.lvl[c] == 1) {
+      l1_by_code[c].push_back(i);
+      P.l1tmp[i] = (int64_t)P.l1_elems;
+      P.l1_elems += (size_t)m[i];
+    } else {
+      big.push_back({c, i});
+    }
   }
   for (int c = 0; c < kNumSizes; ++c)
     if (used[c]) {

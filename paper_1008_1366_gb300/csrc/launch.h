@@ -23,6 +23,14 @@ struct DeviceInfo {
 const DeviceInfo& device_info();
 
 dc_status launch_conv1d(int kind, int dsize, const ConvArgs& a, int grid, int smem, cudaStream_t s);
+
+// Uniform batches (n instances of size m at stride m) of the binary complex
+// convolution on the fixed-shape engine (batched.cu): whether m qualifies,
+// the workspace bytes (host-only), and the cached plan (created on first use).
+bool fx_uniform_ok(int64_t m, int ds);
+bool fx_uniform_two_level(int64_t m);   // m runs as row/column passes spread over many blocks
+size_t fx_uniform_work(int64_t n, int64_t m, int ds);
+dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, struct dc_batched_plan** out);
 dc_status conv1d_blocks_per_sm(int kind, int dsize, int smem, int* out);
 
 }  // namespace dc

@@ -41,6 +41,8 @@ struct Md {
   int64_t S = 0;              // 3D: slabs per chunk
   AxisArgs ax, ay;            // outer-axis templates (plan, tile width, table)
   CfgDev rows;                // row configuration
+  bool rows_fx = false;       // rows on the fixed-shape engine (binary complex, size in the set)
+  int64_t rows_n[2] = {0, 0}; // row counts of the row launches (full chunk, last chunk)
   int rows_grid = 1;
   size_t rows_slot = 0;
   size_t off_y = 0, off_rows = 0, total = 0;
@@ -122,13 +124,35 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   md->off_y = off;
   if (ndim == 3) off += align_up((size_t)md->narr * md->qa * md->S * my * mlast * ds, 256);
   md->off_rows = off;
-  off += (size_t)md->rows_grid * md->rows_slot;
+  size_t rows_bytes = (size_t)md->rows_grid * md->rows_slot;
+  // binary complex rows of a size in the set run on the fixed-shape engine
+  md->rows_n[0] = nrows;
+  md->rows_n[1] = ndim == 3 && md->slabs % md->S ? md->qa * (md->slabs % md->S) * my : nrows;
+  md->rows_fx = md->row_kind == K_COMPLEX && fx_uniform_ok(mlast, ds);
+  if (md->rows_fx) {
+    rows_bytes = std::max(fx_uniform_work(md->rows_n[0], mlast, ds), fx_uniform_work(md->rows_n[1], mlast, ds));
+    if (with_tables) {
+      for (int k = 0; k < 2; ++k) {
+        dc_batched_plan* p = nullptr;
+        dc_status st = fx_uniform_plan(md->rows_n[k], mlast, ds, &p);
+        if (st != DC_OK) return st;
+      }
+    }
+  }
+  off += align_up(rows_bytes, 256);
   md->total = off;
   return DC_OK;
 }
 
 dc_status run_rows(const Md& md, const void* const* in, void* const* out, int64_t nrows, char* work,
                    cudaStream_t s) {
+  if (md.rows_fx) {
+    // the rows' own status header sits at the start of their region
+    dc_batched_plan* p = nullptr;
+    dc_status st = fx_uniform_plan(nrows, md.m[md.ndim - 1], md.ds, &p);
+    if (st != DC_OK) return st;
+    return dc_conv_complex_1d_batched(p, in[0], in[1], out[0], work + md.off_rows, md.total - md.off_rows, s);
+  }
   ConvArgs a{};
   for (int x = 0; x < 3; ++x) a.in[x] = in[x];
   for (int o = 0; o < 2; ++o) a.out[o] = out[o];

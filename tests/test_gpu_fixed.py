@@ -233,3 +233,18 @@ def test_host_pipeline_runtime_engine(dc):
     plan.run_from_host(hf, hg, hh, df, dg, dh, work, 2)
     torch.cuda.synchronize()
     check_all(sizes, f, g, off, hh.numpy(), torch.complex128)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_in_place(dc, dtype):
+    # h may be f or g: every instance reads its inputs before writing h
+    sizes = [64, 640, 4096, 12288, 65536, 96] * 3
+    f, g, off = synthetic.batched_inputs(sizes, 33)
+    plan = dc.BatchedPlan(sizes, dtype=dtype)
+    for target in ("f", "g"):
+        tf = torch.tensor(f, dtype=dtype, device="cuda")
+        tg = torch.tensor(g, dtype=dtype, device="cuda")
+        out = tf if target == "f" else tg
+        plan(tf, tg, out=out)
+        torch.cuda.synchronize()
+        check_all(sizes, f, g, off, out.cpu().numpy(), dtype)
