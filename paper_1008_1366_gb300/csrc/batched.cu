@@ -223,6 +223,7 @@ fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void*
   a.scratch = (char*)work + p->cnt_bytes;
   a.tmp = (char*)work + fx_tmp_offset(p);
   a.l1tmp = p->d_l1tmp;
+  a.in_place = (h == f || h == g) ? 1 : 0;
   a.wait_limit = fx::kWaitLimit;
   for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
   return a;

@@ -49,8 +49,9 @@ struct FxArgs {
   uint32_t* cnt;           // dependency counters, zero before each launch
   WorkHeader* hdr;         // status word and queue counter, zero before each launch
   void* scratch;
-  void* tmp;               // level-1 partial outputs (residue 0), tmp + l1tmp[instance]
-  const int64_t* l1tmp;
+  void* tmp;               // level-1 partial outputs (residue 0) of in-place calls,
+  const int64_t* l1tmp;    // tmp + l1tmp[instance]; others keep them in h
+  int32_t in_place;        // h is f or g
   long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
   const void* tab[kNumSizes];     // root tables zeta_{2m}^i, i < 2m, per size code
 };

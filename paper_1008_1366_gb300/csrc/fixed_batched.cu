@@ -117,9 +117,10 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
   const C* f = (const C*)a->f + off;
   const C* g = (const C*)a->g + off;
   C* h = (C*)a->h + off;
-  // residue 0's partial output goes to a region of the workspace, so h is
-  // written once, at residue 1, after every read of f and g (in-place calls)
-  C* hp = (C*)a->tmp + (act ? a->l1tmp[a->order[first + gi]] : 0);
+  // Residue 0's partial output: in h itself, or, when h is f or g (in-place
+  // calls), in a region of the workspace, so that h is written only at
+  // residue 1, after every read of f and g.
+  C* hp = a->in_place ? (C*)a->tmp + (act ? a->l1tmp[a->order[first + gi]] : 0) : h;
   C* A = sm + gi * GS;
   C* B = A + PL;
   const Real sc = (Real)1 / (Real)(2 * M);
