@@ -18,8 +18,9 @@ LIB = os.path.join(HERE, "libdealias.so")
 
 SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu"]
 # the fixed-shape engine, one translation unit per precision
-FIXED = [("fixed_batched_f.o", ["-DDC_FX_P=f32", "-DDC_FX_C=float2"]),
-         ("fixed_batched_d.o", ["-DDC_FX_P=f64", "-DDC_FX_C=double2"])]
+FIXED = [(src, src.replace(".cu", f"_{tag}.o"), [f"-DDC_FX_P={ns}", f"-DDC_FX_C={c}"])
+         for src in ("fixed_batched.cu", "fixed_axis.cu")
+         for tag, ns, c in (("f", "f32", "float2"), ("d", "f64", "double2"))]
 # the fused 1D kernel, one translation unit per (kind, precision)
 INSTANCES = [(k, tag, c) for k in range(6) for tag, c in (("f", "float2"), ("d", "double2"))]
 
@@ -29,8 +30,8 @@ def _units():
     for k, tag, c in INSTANCES:
         units.append(("conv1d_inst.cu", f"conv1d_k{k}_{tag}.o",
                       [f"-DDC_INST_KIND={k}", f"-DDC_INST_C={c}", f"-DDC_INST_TAG={tag}"]))
-    for obj, defs in FIXED:
-        units.append(("fixed_batched.cu", obj, defs))
+    for src, obj, defs in FIXED:
+        units.append((src, obj, defs))
     return units
 
 

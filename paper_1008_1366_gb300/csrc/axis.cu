@@ -170,6 +170,10 @@ __global__ void __launch_bounds__(512) axis_forward_kernel(AxisArgs a) {
 }
 
 dc_status launch_axis(bool forward, int dsize, const AxisArgs& a, int narrays, cudaStream_t s) {
+  // axis lengths with compile-time code (fixed_axis.cu) run there
+  const dc_status fst = dsize == 8 ? fx::f32::launch_axis_fixed(forward, a, narrays, s)
+                                   : fx::f64::launch_axis_fixed(forward, a, narrays, s);
+  if (fst != DC_ERR_SIZE) return fst;
   const int64_t tiles = a.outer * ((a.inner + a.w - 1) / a.w);
   if (tiles < 1 || narrays < 1) return DC_OK;
   if (tiles > 0x7fffffff) return DC_ERR_SIZE;

@@ -1,0 +1,306 @@
+// Outer-axis implicit transforms of the multi-dimensional convolutions on
+// the fixed-shape column transforms (fixed.cuh), for axis lengths m = 2^a,
+// 64 <= m <= 4096.  Same contract as axis.cu (Sec. 3: Functions cconv2,
+// conv2, cconv3 and the 3D centered Hermitian case):
+//   complex  (q = 2): residue r = 0, 1 input zeta_{2m}^{rk} U_k (Eq. (2.1)),
+//            forward recombination Eq. (2.2);
+//   centered (q = 3): axis holds 2m-1 values, origin at m-1; residue
+//            r = -1, 0, 1 input w_{k,r} of Eqs. (2.4)-(2.5); forward Eq. (2.6)
+//            for k = -m+1..m-1.
+// A block of 256 threads owns one outer index and a tile of W consecutive
+// inner indices (columns); W = 256 E / m, T = m / E threads per column.
+// Every stage is compile-time code on registers (no runtime plan), the
+// input columns are read once for all residues, and the forward direction
+// recombines the residues in shared memory before one scaled write.
+// Hermitian data: the self-conjugate subspace is projected while loading
+// (or doubled for an upstream gradient, `dbl`), and forward outputs of
+// gradients are halved there (`halve`), as in axis.cu.
+#include "fixed.cuh"
+#include "launch.h"
+#include "multid.h"
+
+namespace dc {
+namespace fx {
+namespace DC_FX_P {
+
+namespace {
+
+constexpr int kAxisE = 16;
+template <int L> struct AxisShape {
+  static constexpr int E = kAxisE;
+  static constexpr int T = L / E;
+  static constexpr int W = kThreads * E / L;
+  static_assert(L % E == 0 && W >= 1 && W * T == kThreads, "axis tile covers the block");
+};
+
+__host__ __device__ constexpr int axis_ceil_log2(int x) {
+  int l = 0;
+  while ((1 << l) < x) ++l;
+  return l;
+}
+
+// shared memory: roots, transform buffer (W L), staged input or
+// recombination buffer ((2m-1) W)
+template <int L> constexpr int axis_smem_bytes() {
+  return (kRootsMax + AxisShape<L>::W * L + (2 * L - 1) * AxisShape<L>::W) * (int)sizeof(C);
+}
+
+__device__ __forceinline__ bool on_selfconj(const AxisArgs& a, int64_t i, int64_t* mirror) {
+  if (a.proj == 2) { *mirror = 0; return i == 0; }                      // 2D: ky = 0 column
+  if (a.proj == 3) {                                                    // 3D: kz = 0 plane
+    if (i % a.proj_mz) return false;
+    const int64_t iy = i / a.proj_mz;
+    *mirror = (a.proj_ny - 1 - iy) * a.proj_mz;
+    return true;
+  }
+  return false;
+}
+
+// element j of column i of the stored axis, projected onto (or, dbl,
+// doubled into) the Hermitian-symmetric subspace on the self-conjugate set
+__device__ __forceinline__ C load_sym(const AxisArgs& a, const C* in, int64_t o, int nin, int j, int64_t i,
+                                      bool dbl) {
+  const C v = in[(o * nin + j) * a.inner + i];
+  int64_t mi;
+  if (!on_selfconj(a, i, &mi)) return v;
+  const C u = in[(o * nin + (nin - 1 - j)) * a.inner + mi];
+  C s;
+  s.x = v.x + u.x;
+  s.y = v.y - u.y;
+  if (!dbl) {
+    s.x *= (Real)0.5;
+    s.y *= (Real)0.5;
+  }
+  return s;
+}
+
+template <int TN>
+__device__ __forceinline__ Roots<C> fill_roots(const AxisArgs& a, C* rts) {
+  constexpr int sh = (axis_ceil_log2(TN) + 1) / 2, nlo = 1 << sh;
+  constexpr int cnt = nlo + (TN + nlo - 1) / nlo;
+  static_assert(cnt <= kRootsMax, "root tables fit their reservation");
+  const C* tab = (const C*)a.tw;
+  for (int e = threadIdx.x; e < cnt; e += kThreads) rts[e] = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
+  __syncthreads();
+  return Roots<C>{rts, rts + nlo, sh, nlo - 1};
+}
+
+template <int L, bool CEN>
+__global__ void __launch_bounds__(kThreads) axis_bwd_kernel(const __grid_constant__ AxisArgs a) {
+  using S = AxisShape<L>;
+  constexpr int E = S::E, W = S::W, TN = (CEN ? 3 : 2) * L, nin = CEN ? 2 * L - 1 : L;
+  using K = Stage<L, E, 0, false>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* rts = (C*)smem_raw;
+  C* buf = rts + kRootsMax;
+  C* stg = buf + W * L;   // centered: the staged input tile, nin rows of W
+  const Roots<C> rt = fill_roots<TN>(a, rts);
+  const int z = blockIdx.y;
+  const C* in = (const C*)a.in[z];
+  const bool dbl = (a.dbl_mask >> z) & 1;
+  const int64_t tiles = (a.inner + W - 1) / W;
+  const int64_t o = blockIdx.x / tiles;
+  const int64_t i0 = (blockIdx.x - o * tiles) * W;
+  const int c = threadIdx.x % W, i = threadIdx.x / W;
+  const int64_t col = i0 + c;
+  const bool act = col < a.inner;
+  C zero;
+  zero.x = 0;
+  zero.y = 0;
+  if constexpr (!CEN) {
+    // the column is read once; residue 1 multiplies it by zeta_{2m}^k
+    C raw[E];
+#pragma unroll
+    for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+      for (int q = 0; q < K::R; ++q)
+        raw[b * K::R + q] = act ? load_sym(a, in, o, nin, pos<L, E, 0, false>(i, b, q), col, dbl) : zero;
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+      C v[E];
+#pragma unroll
+      for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+        for (int q = 0; q < K::R; ++q) {
+          const int e = b * K::R + q;
+          v[e] = r ? cmul(raw[e], rt.at(pos<L, E, 0, false>(i, b, q))) : raw[e];
+        }
+      C* out = (C*)a.out[z * 3 + r] + o * (int64_t)L * a.inner + col;
+      column<L, E, W, TN, false>(v, i, buf + c, rt, [&](int j, int, C y) {
+        if (act) out[(int64_t)j * a.inner] = y;
+      });
+      __syncthreads();
+    }
+  } else {
+    // stage the 2m-1 stored rows of the tile once (coalesced rows of W)
+    for (int e = threadIdx.x; e < nin * W; e += kThreads) {
+      const int j = e / W, cc = e - j * W;
+      stg[e] = i0 + cc < a.inner ? load_sym(a, in, o, nin, j, i0 + cc, dbl) : zero;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int ri = 0; ri < 3; ++ri) {
+      const int r = ri - 1;
+      C v[E];
+#pragma unroll
+      for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+        for (int q = 0; q < K::R; ++q) {
+          // w_{k,r} = U_0 at k = 0, else zeta_{3m}^{rk} (U_k + zeta_3^{-r} U_{k-m})
+          const int k = pos<L, E, 0, false>(i, b, q);
+          C x = stg[(k + L - 1) * W + c];
+          if (k > 0) {
+            const C u = stg[(k - 1) * W + c];
+            if (r == 0) {
+              x = cadd(x, u);
+            } else {
+              C z3;
+              z3.x = (Real)-0.5;
+              z3.y = (Real)(-r) * (Real)0.86602540378443864676;
+              x = cadd(x, cmul(u, z3));
+              const C t = rt.at(k);
+              x = r > 0 ? cmul(x, t) : cmulc(x, t);
+            }
+          }
+          v[b * K::R + q] = x;
+        }
+      C* out = (C*)a.out[z * 3 + ri] + o * (int64_t)L * a.inner + col;
+      column<L, E, W, TN, false>(v, i, buf + c, rt, [&](int j, int, C y) {
+        if (act) out[(int64_t)j * a.inner] = y;
+      });
+      __syncthreads();
+    }
+  }
+}
+
+template <int L, bool CEN>
+__global__ void __launch_bounds__(kThreads) axis_fwd_kernel(const __grid_constant__ AxisArgs a) {
+  using S = AxisShape<L>;
+  constexpr int E = S::E, W = S::W, q = CEN ? 3 : 2, TN = q * L, nout = CEN ? 2 * L - 1 : L;
+  using K = Stage<L, E, 0, true>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* rts = (C*)smem_raw;
+  C* buf = rts + kRootsMax;
+  C* H = buf + W * L;   // centered: the recombined outputs, nout rows of W
+  const Roots<C> rt = fill_roots<TN>(a, rts);
+  const int z = blockIdx.y;
+  const int64_t tiles = (a.inner + W - 1) / W;
+  const int64_t o = blockIdx.x / tiles;
+  const int64_t i0 = (blockIdx.x - o * tiles) * W;
+  const int c = threadIdx.x % W, i = threadIdx.x / W;
+  const int64_t col = i0 + c;
+  const bool act = col < a.inner;
+  const Real scale = (Real)1 / (Real)(q * L);
+  int64_t mi;
+  const bool halve = ((a.halve_mask >> z) & 1) && act && on_selfconj(a, col, &mi);
+  const Real sc = halve ? scale * (Real)0.5 : scale;
+  C zero;
+  zero.x = 0;
+  zero.y = 0;
+  if constexpr (!CEN) {
+    // both residues' columns in registers; residue 0's output stays there
+    C vin[2][E];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const C* src = (const C*)a.fin[z * 3 + r] + o * (int64_t)L * a.inner + col;
+#pragma unroll
+      for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+        for (int qq = 0; qq < K::R; ++qq)
+          vin[r][b * K::R + qq] = act ? src[(int64_t)pos<L, E, 0, true>(i, b, qq) * a.inner] : zero;
+    }
+    C y0[E];
+    column<L, E, W, TN, true>(vin[0], i, buf + c, rt, [&](int, int e, C y) { y0[e] = y; });
+    __syncthreads();
+    C* out = (C*)a.fout[z] + o * (int64_t)L * a.inner + col;
+    column<L, E, W, TN, true>(vin[1], i, buf + c, rt, [&](int k, int e, C y) {
+      // Eq. (2.2): (S_0(k) + zeta_{2m}^{-k} S_1(k)) / 2m
+      if (act) out[(int64_t)k * a.inner] = cscale(cadd(y0[e], cmulc(y, rt.at(k))), sc);
+    });
+  } else {
+#pragma unroll 1
+    for (int ri = 0; ri < 3; ++ri) {
+      const int r = ri - 1;
+      const C* src = (const C*)a.fin[z * 3 + ri] + o * (int64_t)L * a.inner + col;
+      C v[E];
+#pragma unroll
+      for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+        for (int qq = 0; qq < K::R; ++qq)
+          v[b * K::R + qq] = act ? src[(int64_t)pos<L, E, 0, true>(i, b, qq) * a.inner] : zero;
+      // S_r(kk) serves the outputs k = kk (row kk + m - 1) and, for kk > 0,
+      // k = kk - m (row kk - 1), each times zeta_{3m}^{-rk} (Eq. (2.6)); the
+      // thread owning kk is the same for every residue
+      column<L, E, W, TN, true>(v, i, buf + c, rt, [&](int kk, int, C y) {
+        C hi = y, lo = y;
+        if (r != 0) {
+          // k = kk >= 0: zeta_{3m}^{-r kk}; k = kk - m < 0: zeta_{3m}^{-r (kk - m)}
+          const C t = rt.at(kk);
+          hi = r > 0 ? cmulc(y, t) : cmul(y, t);
+          const C u = rt.at(L - kk);
+          lo = r > 0 ? cmul(y, u) : cmulc(y, u);
+        }
+        C* h1 = &H[(kk + L - 1) * W + c];
+        *h1 = ri ? cadd(*h1, hi) : hi;
+        if (kk > 0) {
+          C* h0 = &H[(kk - 1) * W + c];
+          *h0 = ri ? cadd(*h0, lo) : lo;
+        }
+      });
+      __syncthreads();
+    }
+    // one scaled write of the tile (coalesced rows of W)
+    C* out = (C*)a.fout[z] + o * (int64_t)nout * a.inner;
+    for (int e = threadIdx.x; e < nout * W; e += kThreads) {
+      const int j = e / W, cc = e - j * W;
+      const int64_t cl = i0 + cc;
+      if (cl < a.inner) {
+        Real s = scale;
+        int64_t mm;
+        if (((a.halve_mask >> z) & 1) && on_selfconj(a, cl, &mm)) s *= (Real)0.5;
+        out[(int64_t)j * a.inner + cl] = cscale(H[e], s);
+      }
+    }
+  }
+}
+
+template <int L>
+dc_status launch_L(bool forward, const AxisArgs& a, int narrays, cudaStream_t s) {
+  using S = AxisShape<L>;
+  const int64_t tiles = a.outer * ((a.inner + S::W - 1) / S::W);
+  if (tiles < 1 || narrays < 1) return DC_OK;
+  if (tiles > 0x7fffffff) return DC_ERR_SIZE;
+  constexpr int smem = axis_smem_bytes<L>();
+  dim3 grid((unsigned)tiles, (unsigned)narrays);
+  if (a.centered) {
+    auto k = forward ? axis_fwd_kernel<L, true> : axis_bwd_kernel<L, true>;
+    DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k<<<grid, kThreads, smem, s>>>(a);
+  } else {
+    auto k = forward ? axis_fwd_kernel<L, false> : axis_bwd_kernel<L, false>;
+    DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k<<<grid, kThreads, smem, s>>>(a);
+  }
+  DC_CUDA_TRY(cudaGetLastError());
+  return DC_OK;
+}
+
+}  // namespace
+
+// DC_ERR_SIZE when the axis length is not one this file compiles
+dc_status launch_axis_fixed(bool forward, const AxisArgs& a, int narrays, cudaStream_t s) {
+  switch (a.m) {
+    case 64: return launch_L<64>(forward, a, narrays, s);
+    case 128: return launch_L<128>(forward, a, narrays, s);
+    case 256: return launch_L<256>(forward, a, narrays, s);
+    case 512: return launch_L<512>(forward, a, narrays, s);
+    case 1024: return launch_L<1024>(forward, a, narrays, s);
+    case 2048: return launch_L<2048>(forward, a, narrays, s);
+    case 4096: return launch_L<4096>(forward, a, narrays, s);
+    default: return DC_ERR_SIZE;
+  }
+}
+
+}  // namespace DC_FX_P
+}  // namespace fx
+}  // namespace dc

@@ -35,6 +35,13 @@ inline int axis_smem(bool forward, int centered, int m, int w, int ds) {
 
 dc_status launch_axis(bool forward, int dsize, const AxisArgs& a, int narrays, cudaStream_t s);
 
+// the outer-axis passes on compile-time column transforms (fixed_axis.cu);
+// DC_ERR_SIZE for axis lengths that file does not compile
+namespace fx {
+namespace f32 { dc_status launch_axis_fixed(bool forward, const AxisArgs& a, int narrays, cudaStream_t s); }
+namespace f64 { dc_status launch_axis_fixed(bool forward, const AxisArgs& a, int narrays, cudaStream_t s); }
+}  // namespace fx
+
 // public multi-D kinds handled by multid.cu
 dc_status md_workspace(int pkind, int ndim, const int64_t* dims, int ds, size_t* bytes);
 dc_status md_prepare(int pkind, int ndim, const int64_t* dims, int ds);
