@@ -43,6 +43,7 @@ struct dc_batched_plan {
   size_t slot = 0, work = 0;
   // fixed-shape engine
   bool fx = false;
+  bool herm = false;   // centered Hermitian rows (internal uniform plans only)
   const struct FxOps* ops = nullptr;
   fx::HostPlan hp;
   fx::Task* d_tasks = nullptr;
@@ -224,6 +225,7 @@ fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void*
   a.tmp = (char*)work + fx_tmp_offset(p);
   a.l1tmp = p->d_l1tmp;
   a.in_place = (h == f || h == g) ? 1 : 0;
+  a.herm = p->herm ? 1 : 0;
   a.wait_limit = fx::kWaitLimit;
   for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
   return a;
@@ -314,8 +316,9 @@ bool fx_build_plain(dc_batched_plan* p, const int64_t* m, int32_t n, const std::
 }
 
 dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const std::vector<int64_t>& off,
-                       int32_t flags) {
+                       int32_t flags, bool herm = false) {
   p->fx = true;
+  p->herm = herm;
   p->ops = p->ds == 8 ? &kFx32 : &kFx64;
   p->off_host = off;
   int bps = 0;
@@ -332,7 +335,7 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
   p->smem = p->hp.smem;
   for (int c : p->hp.codes) {
     const void* tw = nullptr;
-    st = get_root_table(2 * p->ops->code_size(c), p->ds, &tw);
+    st = get_root_table((herm ? 3 : 2) * p->ops->code_size(c), p->ds, &tw);
     if (st != DC_OK) return st;
     p->tabs[c] = tw;
   }
@@ -723,7 +726,7 @@ dc_status dc_batched_plan_destroy(dc_batched_plan* p) {
 namespace dc {
 namespace {
 std::mutex g_umu;
-std::map<std::tuple<int, int64_t, int64_t, int>, dc_batched_plan*> g_uplans;
+std::map<std::tuple<int, int64_t, int64_t, int, bool>, dc_batched_plan*> g_uplans;
 }  // namespace
 
 bool fx_uniform_ok(int64_t m, int ds) { return (ds == 8 || ds == 16) && fx::f32::size_code(m) >= 0; }
@@ -736,7 +739,27 @@ bool fx_uniform_two_level(int64_t m) {
   return lv == 2;
 }
 
+namespace {
+std::map<std::tuple<int, int64_t, int64_t, int>, size_t> g_uwork;   // (device, n, m, ds) -> bytes
+}  // namespace
+
+size_t fx_uniform_work_uncached(int64_t n, int64_t m, int ds);
+
+// cached: the query runs on every multi-D and 1D call
 size_t fx_uniform_work(int64_t n, int64_t m, int ds) {
+  const auto key = std::make_tuple(device_info().device, n, m, ds);
+  {
+    std::lock_guard<std::mutex> lock(g_umu);
+    auto it = g_uwork.find(key);
+    if (it != g_uwork.end()) return it->second;
+  }
+  const size_t b = fx_uniform_work_uncached(n, m, ds);
+  std::lock_guard<std::mutex> lock(g_umu);
+  g_uwork[key] = b;
+  return b;
+}
+
+size_t fx_uniform_work_uncached(int64_t n, int64_t m, int ds) {
   const FxOps* ops = ds == 8 ? &kFx32 : &kFx64;
   int smem_all = 0;
   for (int c = 0; c < fx::kNumSizes; ++c) smem_all = std::max(smem_all, ops->code_smem(c));
@@ -751,17 +774,35 @@ size_t fx_uniform_work(int64_t n, int64_t m, int ds) {
          hp.l1_elems * (size_t)ds;
 }
 
-dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, dc_batched_plan** out) {
+dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, dc_batched_plan** out, bool herm) {
   int dev = 0;
   DC_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(g_umu);
-  auto key = std::make_tuple(dev, n, m, ds);
+  auto key = std::make_tuple(dev, n, m, ds, herm);
   auto it = g_uplans.find(key);
   if (it != g_uplans.end()) { *out = it->second; return DC_OK; }
   std::vector<int64_t> ms((size_t)n, m);
   dc_batched_plan* p = nullptr;
-  dc_status st = dc_batched_plan_create(ms.data(), (int32_t)n, ds == 8 ? DC_C64 : DC_C128, 0, &p);
-  if (st != DC_OK) return st;
+  if (!herm) {
+    dc_status st = dc_batched_plan_create(ms.data(), (int32_t)n, ds == 8 ? DC_C64 : DC_C128, 0, &p);
+    if (st != DC_OK) return st;
+  } else {
+    // Hermitian rows: level-1 sizes only (their 3m root tables fit the
+    // kernel's shared-memory reservation)
+    if (fx_uniform_two_level(m)) return DC_ERR_SIZE;
+    p = new dc_batched_plan();
+    p->dtype = ds == 8 ? DC_C64 : DC_C128;
+    p->ds = ds;
+    p->n = (int32_t)n;
+    std::vector<int64_t> off((size_t)n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) off[i + 1] = off[i] + m;
+    p->total = off[n];
+    p->m_host = ms;
+    p->off_host = off;
+    DC_CUDA_TRY(cudaGetDevice(&p->device));
+    dc_status st = create_fixed(p, ms.data(), (int32_t)n, off, 0, true);
+    if (st != DC_OK) { dc_batched_plan_destroy(p); return st; }
+  }
   g_uplans[key] = p;
   *out = p;
   return DC_OK;

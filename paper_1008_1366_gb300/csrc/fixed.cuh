@@ -448,6 +448,55 @@ __device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, cons
 }
 
 // ---------------------------------------------------------------------------
+// one residue of a centered Hermitian convolution (Sec. 2.3) on a thread
+// group: a single array holds w^f + i w^g (both transforms are real), so
+// one backward transform gives u^f (real part) and u^g (imaginary part);
+// their product, a real array, takes one forward transform.  ld(x, e) gives
+// the packed input at natural index x; st(x, e, v) takes the output.
+// ---------------------------------------------------------------------------
+template <int L, int E, int TN, class Ld, class St, class Sy>
+__device__ __forceinline__ void conv1_residue(int i, C* Ap, const Roots<C>& rt, const Ld& ld, const St& st,
+                                              const Sy& sync) {
+  using F = Fft<L, E>;
+  constexpr int n = F::n;
+  static_assert(n >= 2, "at least two stages");
+  const Contig A{Ap};
+  C v[E];
+  {
+    using K = Stage<L, E, 0, false>;
+#pragma unroll
+    for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+      for (int q = 0; q < K::R; ++q) v[b * K::R + q] = ld(pos<L, E, 0, false>(i, b, q), b * K::R + q);
+  }
+  dft<L, E, 0, false, TN>(v, i, rt);
+  scatter<L, E, 0, false>(v, i, A);
+  sync();
+  one_middle<L, E, TN, false, 1>(v, i, true, A, rt, sync);
+  // last backward stage (thread-private positions), the real product and
+  // the first forward stage in registers
+  gather<L, E, n - 1, false>(v, i, A);
+  dft<L, E, n - 1, false, TN>(v, i, rt);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    v[e].x = v[e].x * v[e].y;
+    v[e].y = 0;
+  }
+  dft<L, E, 0, true, TN>(v, i, rt);
+  sync();
+  scatter<L, E, 0, true>(v, i, A);
+  sync();
+  one_middle<L, E, TN, true, 1>(v, i, true, A, rt, sync);
+  gather<L, E, n - 1, true>(v, i, A);
+  dft<L, E, n - 1, true, TN>(v, i, rt);
+  using KF = Stage<L, E, n - 1, true>;
+#pragma unroll
+  for (int b = 0; b < KF::NB; ++b)
+#pragma unroll
+    for (int q = 0; q < KF::R; ++q) st(pos<L, E, n - 1, true>(i, b, q), b * KF::R + q, v[b * KF::R + q]);
+}
+
+// ---------------------------------------------------------------------------
 // one L-point column transform of a tile (passes A and C).  v holds the
 // inputs of stage 0 in gather order; st(x, e, v) takes output x (register e).  D: this
 // thread's column of the interleaved tile.  Every thread calls this.

@@ -52,6 +52,7 @@ struct FxArgs {
   void* tmp;               // level-1 partial outputs (residue 0) of in-place calls,
   const int64_t* l1tmp;    // tmp + l1tmp[instance]; others keep them in h
   int32_t in_place;        // h is f or g
+  int32_t herm;            // 1: centered Hermitian convolutions (level-1 sizes only), tables of zeta_{3m}
   long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
   const void* tab[kNumSizes];     // root tables zeta_{2m}^i, i < 2m, per size code
 };

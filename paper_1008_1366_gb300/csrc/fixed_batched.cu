@@ -168,6 +168,73 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
   }
 }
 
+// level 1, centered Hermitian (Sec. 2.3, N = 3m): residue ri (r = ri - 1)
+// of `count` instances.  The input of residue r is
+// w_{k,r} = zeta_{3m}^{rk} (U_k + zeta_3^{-r} conj U_{m-k}) for k > 0 and
+// Re U_0 at k = 0 (Eqs. (2.4)-(2.5) with Hermitian symmetry, U_0 taken
+// real), packed as w^f + i w^g; the output adds zeta_{3m}^{-rk} S_r(k) / 3m
+// (Eq. (2.7)) for k < m.
+template <int M>
+__device__ __noinline__ void l1_herm_residue(const FxArgs* a, int ri, int first, int count, C* sm, Roots<C> rt) {
+  using S = Shape<M>;
+  constexpr int E = S::E, T = S::T, GS = group_stride(M, T), TN = 3 * M;
+  const int gi = threadIdx.x / T, i = threadIdx.x % T;
+  const bool act = gi < count;
+  const int64_t off = act ? a->off[a->order[first + gi]] : 0;
+  const C* f = (const C*)a->f + off;
+  const C* g = (const C*)a->g + off;
+  C* h = (C*)a->h + off;
+  C* hp = a->in_place ? (C*)a->tmp + (act ? a->l1tmp[a->order[first + gi]] : 0) : h;
+  C* A = sm + gi * GS;
+  const Real sc = (Real)1 / (Real)(3 * M);
+  const GroupSync<T> sync{1 + gi};
+  const int r = ri - 1;
+  C z3;
+  z3.x = (Real)-0.5;
+  z3.y = (Real)(-r) * (Real)0.86602540378443864676;
+  auto wk = [&](const C* u, int x) {
+    C w;
+    if (x == 0) {
+      w = __ldg(u);
+      w.y = 0;
+      return w;
+    }
+    C p = __ldg(u + x), q = __ldg(u + (M - x));
+    q.y = -q.y;
+    if (r == 0) return cadd(p, q);
+    w = cadd(p, cmul(q, z3));
+    const C t = rt.at(x);
+    return r > 0 ? cmul(w, t) : cmulc(w, t);
+  };
+  conv1_residue<M, E, TN>(
+      i, A, rt,
+      [&](int x, int) {
+        if (!act) {
+          C z;
+          z.x = 0;
+          z.y = 0;
+          return z;
+        }
+        const C wf = wk(f, x), wg = wk(g, x);
+        C v;   // w^f + i w^g
+        v.x = wf.x - wg.y;
+        v.y = wf.y + wg.x;
+        return v;
+      },
+      [&](int x, int, C v) {
+        if (!act) return;
+        if (r != 0) {
+          const C t = rt.at(x);
+          v = r > 0 ? cmulc(v, t) : cmul(v, t);
+        }
+        v = cscale(v, sc);
+        if (ri == 0) hp[x] = v;
+        else if (ri == 1) hp[x] = cadd(hp[x], v);
+        else h[x] = cadd(hp[x], v);
+      },
+      sync);
+}
+
 // pass A: column tile `tile` of level-2 instance l.  Each pass is its own
 // function so that registers are allocated per pass.
 template <int M>
@@ -301,6 +368,14 @@ __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Root
 template <int M>
 __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C* sm, Roots<C> rt) {
   if constexpr (Shape<M>::l1) {
+    if (a->herm) {
+#pragma unroll 1
+      for (int ri = 0; ri < 3; ++ri) {
+        l1_herm_residue<M>(a, ri, x, y, sm, rt);
+        __syncthreads();
+      }
+      return;
+    }
     l1_residue<M, 0>(a, x, y, sm, rt);
     __syncthreads();
     l1_residue<M, 1>(a, x, y, sm, rt);
@@ -366,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
     const int code = t.kc & 255, type = t.kc >> 8;
     if (code != cur) {
       // lo = zeta_TN^b (b < 2^sh), hi = zeta_TN^(a 2^sh), from the full table
-      const int TN = 2 * size_of_code(code);
+      const int TN = (a.herm ? 3 : 2) * size_of_code(code);
       const int sh = roots_sh(TN), nlo = 1 << sh, cnt = roots_count(TN);
       const C* tab = (const C*)a.tab[code];
       for (int e = threadIdx.x; e < cnt; e += kThreads) rts[e] = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));

@@ -30,7 +30,8 @@ dc_status launch_conv1d(int kind, int dsize, const ConvArgs& a, int grid, int sm
 bool fx_uniform_ok(int64_t m, int ds);
 bool fx_uniform_two_level(int64_t m);   // m runs as row/column passes spread over many blocks
 size_t fx_uniform_work(int64_t n, int64_t m, int ds);
-dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, struct dc_batched_plan** out);
+// herm: centered Hermitian convolutions (level-1 sizes only)
+dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, struct dc_batched_plan** out, bool herm = false);
 dc_status conv1d_blocks_per_sm(int kind, int dsize, int smem, int* out);
 
 }  // namespace dc

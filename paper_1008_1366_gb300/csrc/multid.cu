@@ -125,16 +125,18 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   if (ndim == 3) off += align_up((size_t)md->narr * md->qa * md->S * my * mlast * ds, 256);
   md->off_rows = off;
   size_t rows_bytes = (size_t)md->rows_grid * md->rows_slot;
-  // binary complex rows of a size in the set run on the fixed-shape engine
+  // binary complex rows of a size in the set, and centered Hermitian rows
+  // of a one-level size, run on the fixed-shape engine
   md->rows_n[0] = nrows;
   md->rows_n[1] = ndim == 3 && md->slabs % md->S ? md->qa * (md->slabs % md->S) * my : nrows;
-  md->rows_fx = md->row_kind == K_COMPLEX && fx_uniform_ok(mlast, ds);
+  md->rows_fx = (md->row_kind == K_COMPLEX && fx_uniform_ok(mlast, ds)) ||
+                (md->row_kind == K_HERMITIAN && fx_uniform_ok(mlast, ds) && !fx_uniform_two_level(mlast));
   if (md->rows_fx) {
     rows_bytes = std::max(fx_uniform_work(md->rows_n[0], mlast, ds), fx_uniform_work(md->rows_n[1], mlast, ds));
     if (with_tables) {
       for (int k = 0; k < 2; ++k) {
         dc_batched_plan* p = nullptr;
-        dc_status st = fx_uniform_plan(md->rows_n[k], mlast, ds, &p);
+        dc_status st = fx_uniform_plan(md->rows_n[k], mlast, ds, &p, md->row_kind == K_HERMITIAN);
         if (st != DC_OK) return st;
       }
     }
@@ -149,7 +151,7 @@ dc_status run_rows(const Md& md, const void* const* in, void* const* out, int64_
   if (md.rows_fx) {
     // the rows' own status header sits at the start of their region
     dc_batched_plan* p = nullptr;
-    dc_status st = fx_uniform_plan(nrows, md.m[md.ndim - 1], md.ds, &p);
+    dc_status st = fx_uniform_plan(nrows, md.m[md.ndim - 1], md.ds, &p, md.row_kind == K_HERMITIAN);
     if (st != DC_OK) return st;
     return dc_conv_complex_1d_batched(p, in[0], in[1], out[0], work + md.off_rows, md.total - md.off_rows, s);
   }

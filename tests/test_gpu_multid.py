@@ -57,6 +57,21 @@ def test_hermitian_nd(dc, ms, dtype):
     assert rel_l2(h, oracle.conv_hermitian(f, g)) <= tol(dtype, np.prod([3 * m for m in ms]))
 
 
+# wide rows: the row convolutions run on the fixed-shape engine (every
+# size family, both precisions)
+HW = [(2, 64), (2, 80), (3, 96), (2, 640), (2, 1536), (2, 4096), (2, 6144), (4, 5120), (2, 3, 256)]
+
+
+@pytest.mark.parametrize("ms", HW)
+@pytest.mark.parametrize("dtype", DT)
+def test_hermitian_nd_wide_rows(dc, ms, dtype):
+    shape = synthetic.hermitian_shape(ms)
+    f = synthetic.hermitian_spectrum(shape, 1.5, 13)
+    g = synthetic.hermitian_spectrum(shape, 1.5, 14)
+    h = dc.conv_hermitian_nd(dev(f, dtype), dev(g, dtype)).cpu().numpy()
+    assert rel_l2(h, oracle.padded_hermitian(f, g)) <= tol(dtype, np.prod([3 * m for m in ms]))
+
+
 @pytest.mark.parametrize("ms", [(4, 6), (3, 4, 5)])
 def test_hermitian_nd_projects_raw_inputs(dc, ms):
     # inputs violating the symmetry on the self-conjugate row/plane are projected
