@@ -43,6 +43,7 @@ struct Md {
   CfgDev rows;                // row configuration
   bool rows_fx = false;       // rows on the fixed-shape engine (binary complex, size in the set)
   int64_t rows_n[2] = {0, 0}; // row counts of the row launches (full chunk, last chunk)
+  size_t off_pair = 0;        // gradient pairs: the temporary rows, inside the rows region
   int rows_grid = 1;
   size_t rows_slot = 0;
   size_t off_y = 0, off_rows = 0, total = 0;
@@ -129,14 +130,24 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   // of a one-level size, run on the fixed-shape engine
   md->rows_n[0] = nrows;
   md->rows_n[1] = ndim == 3 && md->slabs % md->S ? md->qa * (md->slabs % md->S) * my : nrows;
+  // Hermitian rows only; the gradient pair (K_HERMITIAN_PAIR) stays on the
+  // runtime-shaped kernel: it transforms W alone and keeps the real part,
+  // which drops any non-Hermitian rounding of W's rows, while two packed
+  // plain convolutions (W + i g) would carry it into g's channel
+  const bool herm_rows = md->row_kind == K_HERMITIAN;
   md->rows_fx = (md->row_kind == K_COMPLEX && fx_uniform_ok(mlast, ds)) ||
-                (md->row_kind == K_HERMITIAN && fx_uniform_ok(mlast, ds) && !fx_uniform_two_level(mlast));
+                (herm_rows && fx_uniform_ok(mlast, ds) && !fx_uniform_two_level(mlast));
   if (md->rows_fx) {
     rows_bytes = std::max(fx_uniform_work(md->rows_n[0], mlast, ds), fx_uniform_work(md->rows_n[1], mlast, ds));
+    // gradient pairs: one temporary array of rows for the second output
+    if (md->row_kind == K_HERMITIAN_PAIR) {
+      md->off_pair = align_up(rows_bytes, 256);
+      rows_bytes = md->off_pair + (size_t)std::max(md->rows_n[0], md->rows_n[1]) * mlast * ds;
+    }
     if (with_tables) {
       for (int k = 0; k < 2; ++k) {
         dc_batched_plan* p = nullptr;
-        dc_status st = fx_uniform_plan(md->rows_n[k], mlast, ds, &p, md->row_kind == K_HERMITIAN);
+        dc_status st = fx_uniform_plan(md->rows_n[k], mlast, ds, &p, herm_rows);
         if (st != DC_OK) return st;
       }
     }
@@ -150,10 +161,23 @@ dc_status run_rows(const Md& md, const void* const* in, void* const* out, int64_
                    cudaStream_t s) {
   if (md.rows_fx) {
     // the rows' own status header sits at the start of their region
+    const int64_t m = md.m[md.ndim - 1];
+    const bool pair = md.row_kind == K_HERMITIAN_PAIR;
     dc_batched_plan* p = nullptr;
-    dc_status st = fx_uniform_plan(nrows, md.m[md.ndim - 1], md.ds, &p, md.row_kind == K_HERMITIAN);
+    dc_status st = fx_uniform_plan(nrows, m, md.ds, &p, md.row_kind != K_COMPLEX);
     if (st != DC_OK) return st;
-    return dc_conv_complex_1d_batched(p, in[0], in[1], out[0], work + md.off_rows, md.total - md.off_rows, s);
+    char* rw = work + md.off_rows;
+    if (!pair) return dc_conv_complex_1d_batched(p, in[0], in[1], out[0], rw, md.total - md.off_rows, s);
+    // gradient rows: dg = conv(W, f) into the temporary, then df = conv(W, g)
+    // over f (no longer read), then dg over g; the same transforms as a
+    // shared-W pair, since each plain convolution packs its two inputs
+    // into one transform
+    const size_t wb = md.off_pair;
+    void* tmp = rw + md.off_pair;
+    if ((st = dc_conv_complex_1d_batched(p, in[0], in[1], tmp, rw, wb, s)) != DC_OK) return st;
+    if ((st = dc_conv_complex_1d_batched(p, in[0], in[2], out[0], rw, wb, s)) != DC_OK) return st;
+    DC_CUDA_TRY(cudaMemcpyAsync(out[1], tmp, (size_t)nrows * m * md.ds, cudaMemcpyDeviceToDevice, s));
+    return DC_OK;
   }
   ConvArgs a{};
   for (int x = 0; x < 3; ++x) a.in[x] = in[x];
