@@ -73,7 +73,7 @@ struct FxOps {
   int64_t (*code_size)(int);
   void (*code_shape)(int, int*, int*, int*, int*, int*);
   int (*code_smem)(int);
-  bool (*build_plan)(const int64_t*, int32_t, const int64_t*, const fx::Schedule&, fx::HostPlan*);
+  bool (*build_plan)(const int64_t*, int32_t, const int64_t*, const fx::Schedule&, bool, fx::HostPlan*);
   dc_status (*prepare_kernel)(int, int*);
   dc_status (*launch)(const fx::FxArgs&, int, int, cudaStream_t);
 };
@@ -289,7 +289,7 @@ bool fx_build_plain(dc_batched_plan* p, const int64_t* m, int32_t n, const std::
   const fx::Schedule sc{p->grid / 2, 0};
   for (int32_t i = 0; i < n; ++i) {
     fx::HostPlan one;
-    if (!p->ops->build_plan(m + i, 1, off.data() + i, sc, &one)) return false;
+    if (!p->ops->build_plan(m + i, 1, off.data() + i, sc, p->herm, &one)) return false;
     const int32_t ob = (int32_t)all.order.size(), lb = (int32_t)all.l2.size(), cb = (int32_t)all.ncnt;
     p->inst_first.push_back((int32_t)all.tasks.size());
     p->inst_count.push_back((int32_t)one.tasks.size());
@@ -330,7 +330,7 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
   p->grid = bps * device_info().sms;
   const fx::Schedule dflt{p->grid / 2, 0};
   const bool plain = (flags & DC_PLAN_ONE_PER_LAUNCH) != 0;
-  if (plain ? !fx_build_plain(p, m, n, off) : !p->ops->build_plan(m, n, off.data(), dflt, &p->hp))
+  if (plain ? !fx_build_plain(p, m, n, off) : !p->ops->build_plan(m, n, off.data(), dflt, p->herm, &p->hp))
     return DC_ERR_SIZE;
   p->smem = p->hp.smem;
   for (int c : p->hp.codes) {
@@ -353,14 +353,14 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
       for (int mode = 0; mode < fx::kL1Modes; ++mode) {
         const fx::Schedule sc{cand, mode};
         if (cand < 1 || (cand == dflt.batch_target && mode == dflt.l1_mode)) continue;
-        if (!p->ops->build_plan(m, n, off.data(), sc, &p->hp) || fx_upload(p, off) != DC_OK) continue;
+        if (!p->ops->build_plan(m, n, off.data(), sc, p->herm, &p->hp) || fx_upload(p, off) != DC_OK) continue;
         const float t = fx_time(p, s);
         if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; best = sc; }
       }
     }
     cudaStreamDestroy(s);
     cudaGetLastError();
-    if (!p->ops->build_plan(m, n, off.data(), best, &p->hp)) return DC_ERR_SIZE;
+    if (!p->ops->build_plan(m, n, off.data(), best, p->herm, &p->hp)) return DC_ERR_SIZE;
     st = fx_upload(p, off);
     if (st != DC_OK) return st;
     p->fx_sched = best;
@@ -564,7 +564,7 @@ dc_status dc_batched_plan_set_schedule(dc_batched_plan* p, int32_t batch_target,
   std::vector<int64_t> ms(p->n);
   for (int32_t i = 0; i < p->n; ++i) ms[i] = p->off_host[i + 1] - p->off_host[i];
   const fx::Schedule sc{batch_target, l1_mode};
-  if (!p->ops->build_plan(ms.data(), p->n, p->off_host.data(), sc, &p->hp)) return DC_ERR_SIZE;
+  if (!p->ops->build_plan(ms.data(), p->n, p->off_host.data(), sc, p->herm, &p->hp)) return DC_ERR_SIZE;
   dc_status st = fx_upload(p, p->off_host);
   if (st != DC_OK) return st;
   p->fx_sched = sc;
@@ -768,7 +768,9 @@ size_t fx_uniform_work_uncached(int64_t n, int64_t m, int ds) {
   for (int64_t i = 0; i < n; ++i) off[i + 1] = off[i] + m;
   fx::HostPlan hp;
   const fx::Schedule sc{bps * device_info().sms / 2, 0};
-  if (!ops->build_plan(ms.data(), (int32_t)n, off.data(), sc, &hp)) return 0;
+  // the workspace of a centered Hermitian plan is the same (same scratch
+  // regions and counters; only the task count differs)
+  if (!ops->build_plan(ms.data(), (int32_t)n, off.data(), sc, false, &hp)) return 0;
   (void)smem_all;
   return align_up(sizeof(WorkHeader) + hp.ncnt * sizeof(uint32_t), 256) + align_up(hp.scratch * (size_t)ds, 256) +
          hp.l1_elems * (size_t)ds;
@@ -787,9 +789,6 @@ dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, dc_batched_plan** out, b
     dc_status st = dc_batched_plan_create(ms.data(), (int32_t)n, ds == 8 ? DC_C64 : DC_C128, 0, &p);
     if (st != DC_OK) return st;
   } else {
-    // Hermitian rows: level-1 sizes only (their 3m root tables fit the
-    // kernel's shared-memory reservation)
-    if (fx_uniform_two_level(m)) return DC_ERR_SIZE;
     p = new dc_batched_plan();
     p->dtype = ds == 8 ? DC_C64 : DC_C128;
     p->ds = ds;

@@ -89,6 +89,10 @@ dc_status check_work(void* work, size_t have, size_t need) {
   return DC_OK;
 }
 
+bool on_fixed_engine(int kind, int64_t m, int ds) {
+  return (kind == K_COMPLEX || kind == K_HERMITIAN) && fx_uniform_ok(m, ds) && fx_uniform_two_level(m);
+}
+
 // Plans one 1D call; fills cfg (with its table) and the workspace size.
 dc_status plan_1d(int kind, int64_t m, int ds, bool with_table, CfgDev* cfg, size_t* work) {
   if (m < 1) return DC_ERR_ARG;
@@ -100,14 +104,15 @@ dc_status plan_1d(int kind, int64_t m, int ds, bool with_table, CfgDev* cfg, siz
     cfg->tw = tw;
   }
   *work = kHeader + align_up(cfg_scratch_bytes(kind, *cfg, ds), 256);
-  // a single binary complex convolution of a two-level size runs on the
-  // fixed-shape engine (a one-instance plan, cached): its passes spread over
-  // many blocks, where the runtime-shaped kernel gives the instance one
-  if (kind == K_COMPLEX && fx_uniform_ok(m, ds) && fx_uniform_two_level(m)) {
+  // a single binary complex or centered Hermitian convolution of a
+  // two-level size runs on the fixed-shape engine (a one-instance plan,
+  // cached): its passes spread over many blocks, where the runtime-shaped
+  // kernel gives the instance one
+  if (on_fixed_engine(kind, m, ds)) {
     *work = std::max(*work, fx_uniform_work(1, m, ds));
     if (with_table) {
       dc_batched_plan* p = nullptr;
-      dc_status st = fx_uniform_plan(1, m, ds, &p);
+      dc_status st = fx_uniform_plan(1, m, ds, &p, kind == K_HERMITIAN);
       if (st != DC_OK) return st;
     }
   }
@@ -126,9 +131,9 @@ dc_status run_1d(int kind, const void* const* ins, int nin, void* const* outs, i
   if (st != DC_OK) return st;
   if ((st = check_work(work, work_bytes, need)) != DC_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if (kind == K_COMPLEX && fx_uniform_ok(m, ds) && fx_uniform_two_level(m)) {
+  if (on_fixed_engine(kind, m, ds)) {
     dc_batched_plan* p = nullptr;
-    if ((st = fx_uniform_plan(1, m, ds, &p)) != DC_OK) return st;
+    if ((st = fx_uniform_plan(1, m, ds, &p, kind == K_HERMITIAN)) != DC_OK) return st;
     return dc_conv_complex_1d_batched(p, ins[0], ins[1], outs[0], work, work_bytes, s);
   }
   ConvArgs a{};

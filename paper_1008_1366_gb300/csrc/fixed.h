@@ -52,7 +52,7 @@ struct FxArgs {
   void* tmp;               // level-1 partial outputs (residue 0) of in-place calls,
   const int64_t* l1tmp;    // tmp + l1tmp[instance]; others keep them in h
   int32_t in_place;        // h is f or g
-  int32_t herm;            // 1: centered Hermitian convolutions (level-1 sizes only), tables of zeta_{3m}
+  int32_t herm;            // 1: centered Hermitian convolutions, tables of zeta_{3m}
   long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
   const void* tab[kNumSizes];     // root tables zeta_{2m}^i, i < 2m, per size code
 };
@@ -90,9 +90,10 @@ constexpr long long kWaitLimit = 1ll << 32;   // about two seconds at 2 GHz
   void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W);           \
   /* dynamic shared memory the kernel needs for a size code */                              \
   int code_smem(int code);                                                                  \
-  /* the task queue for n instances of sizes m[i] at element offsets off[i] */              \
+  /* the task queue for n instances of sizes m[i] at element offsets off[i]; herm: */     \
+  /* centered Hermitian convolutions (three residues: more row tasks per instance) */       \
   bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc,     \
-                  HostPlan* out);                                                           \
+                  bool herm, HostPlan* out);                                                \
   /* kernel attributes, occupancy */                                                        \
   dc_status prepare_kernel(int smem, int* blocks_per_sm);                                   \
   dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s);

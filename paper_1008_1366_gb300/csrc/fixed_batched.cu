@@ -62,9 +62,6 @@ __host__ __device__ constexpr int roots_sh(int TN) { return (ceil_log2(TN) + 1) 
 __host__ __device__ constexpr int roots_count(int TN) {
   return (1 << roots_sh(TN)) + (TN + (1 << roots_sh(TN)) - 1) / (1 << roots_sh(TN));
 }
-static_assert(roots_count(131072) <= kRootsMax, "root table fits its reservation");
-static_assert(roots_count(98304) <= kRootsMax, "root table fits its reservation");
-static_assert(roots_count(81920) <= kRootsMax, "root table fits its reservation");
 
 constexpr int kBlocksPerSM = kDouble ? 1 : 2;
 
@@ -85,8 +82,10 @@ template <int M> struct Shape {
   static constexpr int GR = kThreads / T1;
   static constexpr int nA = L1 / W;
   static constexpr int nB = 2 * L2 / GR;
+  static constexpr int nBh = 3 * L2 / GR;   // centered Hermitian: three residues, one packed row each
   static constexpr int EC = l1 ? 16 : col_E(M);
-  static_assert(l1 || (L1 % W == 0 && (2 * L2) % GR == 0 && L1 * L2 == M), "level-2 tiling must be exact");
+  static_assert(l1 || (L1 % W == 0 && (2 * L2) % GR == 0 && (3 * L2) % GR == 0 && L1 * L2 == M),
+                "level-2 tiling must be exact");
   static_assert(!l1 || kThreads % T == 0, "level-1 groups must tile the block");
   static constexpr int CB = (int)sizeof(C);
   // level 2: the row groups of pass B, or two column tiles (the transform
@@ -94,10 +93,20 @@ template <int M> struct Shape {
   static constexpr int smem = l1 ? G * group_stride(M, T) * CB
                                  : (GR * group_stride(L1, T1) * CB > 2 * W * L2 * CB ? GR * group_stride(L1, T1) * CB
                                                                                        : 2 * W * L2 * CB);
+  // Root tables: kRootsMax entries at the start of shared memory, enough
+  // for zeta_{2m} of every size and zeta_{3m} of the level-1 sizes.  The
+  // high half of the zeta_{3m} tables of the Hermitian level-2 sizes goes
+  // behind the task data instead.
+  static constexpr int herm_roots = roots_count(3 * M);
+  static constexpr int herm_lo = 1 << roots_sh(3 * M);
+  static constexpr bool herm_behind = !l1 && herm_roots > kRootsMax;
+  static constexpr int herm_off = kRootsMax * CB + (smem + 15) / 16 * 16;   // bytes from the start
+  static constexpr int total = kRootsMax * CB + smem + (herm_behind ? 16 + (herm_roots - herm_lo) * CB : 0);
+  static_assert(herm_lo <= kRootsMax, "low root table fits its reservation");
+  static_assert(roots_count(2 * M) <= kRootsMax && (!l1 || herm_roots <= kRootsMax), "root tables fit");
   // FP32: two blocks per SM, FP64: one (228 KB per SM less 1 KB reserved per
   // block and the static shared variables)
-  static_assert(smem + kRootsMax * CB <= (233472 - kBlocksPerSM * 1024) / kBlocksPerSM - 64,
-                "the blocks fit on an SM");
+  static_assert(total <= (233472 - kBlocksPerSM * 1024) / kBlocksPerSM - 64, "the blocks fit on an SM");
 };
 
 // ---------------------------------------------------------------------------
@@ -365,6 +374,133 @@ __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Root
   }
 }
 
+// Level 2 of a centered Hermitian convolution (Sec. 2.3, N = 3m): the three
+// residues r = -1, 0, 1 each hold one packed array w^f + i w^g (both
+// backward transforms are real), in scratch arrays ri = r + 1.
+//
+// pass A: column tile `tile` of level-2 instance l.  With P_k = f_k + i g_k
+// and Q_k = conj f_{m-k} + i conj g_{m-k}, residue r's packed input is
+// zeta_{3m}^{rk} (P_k + zeta_3^{-r} Q_k) (Eqs. (2.4)-(2.5) with Hermitian
+// symmetry); at k = 0 it is Re f_0 + i Re g_0 for every r.
+template <int M>
+__device__ __noinline__ void run_A_herm(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
+  using S = Shape<M>;
+  constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 3 * M;
+  using K = Stage<L2, E, 0, false>;
+  const int c = threadIdx.x % W, i = threadIdx.x / W;
+  const int k1 = tile * W + c;
+  const L2Inst in = a->l2[l];
+  C* scr = (C*)a->scratch + in.scr;
+  const C* f = (const C*)a->f + in.off;
+  const C* g = (const C*)a->g + in.off;
+  C P[E], Q[E];
+#pragma unroll
+  for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+    for (int q = 0; q < K::R; ++q) {
+      const int e = b * K::R + q;
+      const int k = k1 + L1 * pos<L2, E, 0, false>(i, b, q);
+      const int mk = k ? M - k : 0;
+      const C fk = __ldg(f + k), gk = __ldg(g + k), fm = __ldg(f + mk), gm = __ldg(g + mk);
+      P[e].x = k ? fk.x - gk.y : fk.x;
+      P[e].y = k ? fk.y + gk.x : gk.x;
+      Q[e].x = k ? fm.x + gm.y : (Real)0;
+      Q[e].y = k ? gm.x - fm.y : (Real)0;
+    }
+#pragma unroll 1
+  for (int ri = 0; ri < 3; ++ri) {
+    const int r = ri - 1;
+    C z3;   // zeta_3^{-r}
+    z3.x = (Real)-0.5;
+    z3.y = (Real)(-r) * (Real)0.86602540378443864676;
+    C v[E];
+#pragma unroll
+    for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+      for (int q = 0; q < K::R; ++q) {
+        const int e = b * K::R + q;
+        C w = r == 0 ? cadd(P[e], Q[e]) : cadd(P[e], cmul(Q[e], z3));
+        if (r != 0) {
+          const C t = rt.at(k1 + L1 * pos<L2, E, 0, false>(i, b, q));
+          w = r > 0 ? cmul(w, t) : cmulc(w, t);
+        }
+        v[e] = w;
+      }
+    // S_r[j2][k1]; the factor zeta_m^{j2 k1} is applied in pass B
+    C* dst = scr + (size_t)ri * M + k1;
+    column<L2, E, W, TN, false>(v, i, sm + c, rt, [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
+    __syncthreads();
+  }
+}
+
+// pass B: row group `unit` (rows (ri, j2), ri = row / L2) of level-2
+// instance l: times zeta_m^{j2 k1}, backward row transform, the real
+// product u^f u^g, forward row transform, times zeta_m^{-j2 k1}, in place
+template <int M>
+__device__ __noinline__ void run_B_herm(const FxArgs* a, int l, int unit, C* sm, Roots<C> rt) {
+  using S = Shape<M>;
+  constexpr int L1 = S::L1, L2 = S::L2, E1 = S::E1, T1 = S::T1, GR = S::GR, GS = group_stride(L1, T1),
+                TN = 3 * M;
+  const int gi = threadIdx.x / T1, i = threadIdx.x % T1;
+  const int row = unit * GR + gi;
+  const int ri = row / L2, j2 = row % L2;
+  C* s = (C*)a->scratch + a->l2[l].scr + (size_t)ri * M + (size_t)j2 * L1;
+  const GroupSync<T1> sync{1 + gi};
+  static_assert(E1 <= 20, "rows hold their twiddles in registers");
+  C tw[E1];
+  conv1_residue<L1, E1, TN>(
+      i, sm + gi * GS, rt,
+      [&](int x, int e) {
+        tw[e] = rt.at(3 * j2 * x);
+        return cmul(__ldcg(s + x), tw[e]);
+      },
+      [&](int x, int e, C v) { __stcg(s + x, cmulc(v, tw[e])); }, sync);
+}
+
+// pass C: column tile `tile` of level-2 instance l: the forward column
+// transforms of the three residues, recombined as
+// h_k = sum_r zeta_{3m}^{-rk} S_r(k) / 3m (Eq. (2.7)), k < m
+template <int M>
+__device__ __noinline__ void run_C_herm(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
+  using S = Shape<M>;
+  constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 3 * M;
+  using K = Stage<L2, E, 0, true>;
+  const int c = threadIdx.x % W, i = threadIdx.x / W;
+  const int k1 = tile * W + c;
+  const L2Inst in = a->l2[l];
+  const C* scr = (const C*)a->scratch + in.scr;
+  C* h = (C*)a->h + in.off + k1;
+  const Real sc = (Real)1 / (Real)(3 * M);
+  C acc[E];
+#pragma unroll 1
+  for (int ri = 0; ri < 3; ++ri) {
+    const int r = ri - 1;
+    const C* src = scr + (size_t)ri * M + k1;
+    C v[E];
+#pragma unroll
+    for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+      for (int q = 0; q < K::R; ++q) v[b * K::R + q] = __ldcg(src + (size_t)L1 * pos<L2, E, 0, true>(i, b, q));
+    column<L2, E, W, TN, true>(v, i, sm + c, rt, [&](int k2, int e, C y) {
+      if (r != 0) {
+        const C t = rt.at(k1 + L1 * k2);
+        y = r > 0 ? cmulc(y, t) : cmul(y, t);
+      }
+      if (ri == 0) acc[e] = y;
+      else if (ri == 1) acc[e] = cadd(acc[e], y);
+      else h[(size_t)L1 * k2] = cscale(cadd(acc[e], y), sc);
+    });
+    __syncthreads();
+  }
+  // the three product columns of the tile were read for the last time
+  constexpr int LPR = W * (int)sizeof(C) / 128;   // 128-byte lines per tile row
+  for (int ln = threadIdx.x; ln < 3 * L2 * LPR; ln += kThreads) {
+    const int rr = ln / (L2 * LPR), rest = ln % (L2 * LPR);
+    const C* row = scr + (size_t)rr * M + (size_t)(rest / LPR) * L1 + (size_t)tile * W;
+    discard_l2((const char*)row + (rest % LPR) * 128);
+  }
+}
+
 template <int M>
 __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C* sm, Roots<C> rt) {
   if constexpr (Shape<M>::l1) {
@@ -380,6 +516,12 @@ __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C
     __syncthreads();
     l1_residue<M, 1>(a, x, y, sm, rt);
   } else {
+    if (a->herm) {
+      if (type == T_A) run_A_herm<M>(a, x, y, sm, rt);
+      else if (type == T_B) run_B_herm<M>(a, x, y, sm, rt);
+      else run_C_herm<M>(a, x, y, sm, rt);
+      return;
+    }
     if (type == T_A) run_A<M>(a, x, y, sm, rt);
     else if (type == T_B) run_B<M>(a, x, y, sm, rt);
     else run_C<M>(a, x, y, sm, rt);
@@ -403,6 +545,22 @@ __device__ __forceinline__ bool wait_geq(const uint32_t* c, uint32_t need, WorkH
     }
     if (dt > limit) return false;
     __nanosleep(256);
+  }
+}
+
+// byte offset of the root tables of size code `code` in shared memory
+__device__ __forceinline__ int roots_off_of(int code, bool herm) {
+  if (!herm) return 0;
+  switch (code) {
+#define DC_FX_OFF(c) \
+    case c: return Shape<size_of_code(c)>::herm_behind ? Shape<size_of_code(c)>::herm_off : 0;
+    DC_FX_OFF(0) DC_FX_OFF(1) DC_FX_OFF(2) DC_FX_OFF(3) DC_FX_OFF(4) DC_FX_OFF(5) DC_FX_OFF(6) DC_FX_OFF(7)
+    DC_FX_OFF(8) DC_FX_OFF(9) DC_FX_OFF(10) DC_FX_OFF(11) DC_FX_OFF(12) DC_FX_OFF(13) DC_FX_OFF(14)
+    DC_FX_OFF(15) DC_FX_OFF(16) DC_FX_OFF(17) DC_FX_OFF(18) DC_FX_OFF(19) DC_FX_OFF(20) DC_FX_OFF(21)
+    DC_FX_OFF(22) DC_FX_OFF(23) DC_FX_OFF(24) DC_FX_OFF(25) DC_FX_OFF(26) DC_FX_OFF(27) DC_FX_OFF(28)
+    DC_FX_OFF(29) DC_FX_OFF(30)
+#undef DC_FX_OFF
+    default: return 0;
   }
 }
 
@@ -444,8 +602,13 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
       const int TN = (a.herm ? 3 : 2) * size_of_code(code);
       const int sh = roots_sh(TN), nlo = 1 << sh, cnt = roots_count(TN);
       const C* tab = (const C*)a.tab[code];
-      for (int e = threadIdx.x; e < cnt; e += kThreads) rts[e] = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
-      rt = Roots<C>{rts, rts + nlo, sh, nlo - 1};
+      // the low table always starts shared memory; the high one follows it,
+      // or sits behind the task data for the Hermitian level-2 sizes
+      const int hoff = roots_off_of(code, a.herm != 0);
+      C* hi = hoff ? (C*)(smem_raw + hoff) : rts + nlo;
+      for (int e = threadIdx.x; e < cnt; e += kThreads)
+        (e < nlo ? rts[e] : hi[e - nlo]) = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
+      rt = Roots<C>{rts, hi, sh, nlo - 1};
       cur = code;
       __syncthreads();
     }
@@ -479,20 +642,21 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
 // ---------------------------------------------------------------------------
 namespace {
 template <int... Cs> struct CodeTable {
-  static void fill(int* lvl, int* per, int* l1, int* l2, int* w, int* na, int* nb, int* smem) {
+  static void fill(int* lvl, int* per, int* l1, int* l2, int* w, int* na, int* nb, int* nbh, int* smem) {
     int k = 0;
     ((lvl[k] = Shape<size_of_code(Cs)>::l1 ? 1 : 2, per[k] = Shape<size_of_code(Cs)>::G,
       l1[k] = Shape<size_of_code(Cs)>::L1, l2[k] = Shape<size_of_code(Cs)>::L2, w[k] = Shape<size_of_code(Cs)>::W,
       na[k] = Shape<size_of_code(Cs)>::nA, nb[k] = Shape<size_of_code(Cs)>::nB,
-      smem[k] = Shape<size_of_code(Cs)>::smem, ++k), ...);
+      nbh[k] = Shape<size_of_code(Cs)>::nBh,
+      smem[k] = Shape<size_of_code(Cs)>::total, ++k), ...);
   }
 };
 struct Tables {
   int lvl[kNumSizes], per[kNumSizes], l1[kNumSizes], l2[kNumSizes], w[kNumSizes], na[kNumSizes],
-      nb[kNumSizes], smem[kNumSizes];
+      nb[kNumSizes], nbh[kNumSizes], smem[kNumSizes];
   Tables() {
     CodeTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
-              26, 27, 28, 29, 30>::fill(lvl, per, l1, l2, w, na, nb, smem);
+              26, 27, 28, 29, 30>::fill(lvl, per, l1, l2, w, na, nb, nbh, smem);
   }
 };
 const Tables& tables() {
@@ -508,7 +672,7 @@ int size_code(int64_t m) {
 }
 int64_t code_size(int code) { return size_of_code(code); }
 bool code_level1(int code) { return tables().lvl[code] == 1; }
-int code_smem(int code) { return tables().smem[code] + kRootsMax * (int)sizeof(C); }
+int code_smem(int code) { return tables().smem[code]; }
 void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W) {
   const Tables& t = tables();
   *level = t.lvl[code];
@@ -518,7 +682,7 @@ void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W) {
   *W = t.lvl[code] == 1 ? 0 : t.w[code];
 }
 
-bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc, HostPlan* out) {
+bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc, bool herm, HostPlan* out) {
   const int batch_target = std::max(1, sc.batch_target);
   const Tables& tb = tables();
   HostPlan& P = *out;
@@ -616,7 +780,8 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   auto emit = [&](int type, int k) {
     for (int l : batches[k]) {
       const int c = big[l].first;
-      const int cnt = type == T_B ? tb.nb[c] : tb.na[c];
+      const int nbc = herm ? tb.nbh[c] : tb.nb[c];
+      const int cnt = type == T_B ? nbc : tb.na[c];
       for (int u = 0; u < cnt; ++u) {
         Task t{(type << 8) | c, l, u, -1, 0, -1};
         if (type == T_A) {
@@ -625,7 +790,7 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
         } else if (type == T_B) {
           t.widx = 2 * l; t.wneed = (uint32_t)tb.na[c]; t.sidx = 2 * l + 1;
         } else {
-          t.widx = 2 * l + 1; t.wneed = (uint32_t)tb.nb[c]; t.sidx = 2 * n2 + k;
+          t.widx = 2 * l + 1; t.wneed = (uint32_t)nbc; t.sidx = 2 * n2 + k;
         }
         P.tasks.push_back(t);
       }

@@ -65,7 +65,9 @@ def test_complex_1d_in_place(dc):
     assert rel_l2(tf.cpu().numpy(), oracle.conv_complex(f, g)) <= FP64_TOL
 
 
-HERM = [1, 2, 4, 6, 8, 10, 12, 16, 20, 24, 40, 48, 64, 96, 160, 256, 1024, 3072, 5120, 8192, 16384, 65536]
+# 8192 and up (in the size set): the fixed-shape engine's two-level passes
+HERM = [1, 2, 4, 6, 8, 10, 12, 16, 20, 24, 40, 48, 64, 96, 160, 256, 1024, 3072, 5120, 8192, 10240, 12288, 16384,
+        20480, 24576, 32768, 40960, 49152, 65536]
 
 
 @pytest.mark.parametrize("m", HERM)
@@ -78,17 +80,31 @@ def test_hermitian_1d(dc, m, dtype):
     assert rel_l2(h, ref) <= tol_for(dtype, 3 * m)
 
 
-def test_hermitian_1d_projection_of_raw_input(dc):
+@pytest.mark.parametrize("m", [256, 16384])
+def test_hermitian_1d_projection_of_raw_input(dc, m):
     # a non-real f_0 is projected to Re f_0, like the oracle
-    m = 256
     f = synthetic.uniform_complex(m, 5)
     g = synthetic.uniform_complex(m, 6)
     h = dc.conv_hermitian_1d(to_dev(f, torch.complex128), to_dev(g, torch.complex128)).cpu().numpy()
     assert rel_l2(h, oracle.conv_hermitian(f, g)) <= FP64_TOL
 
 
-def test_hermitian_1d_paper_closed_form(dc):
-    m = 4096
+@pytest.mark.parametrize("m", [1024, 24576])
+@pytest.mark.parametrize("dtype", [d for d, _ in DTYPES])
+def test_hermitian_1d_in_place(dc, m, dtype):
+    # h may be f or g: every read of the inputs precedes the first write of h
+    f = synthetic.hermitian_spectrum((m,), 1.0, 31)
+    g = synthetic.hermitian_spectrum((m,), 1.0, 32)
+    ref = oracle.conv_hermitian(f, g)
+    for target in ("f", "g"):
+        tf, tg = to_dev(f, dtype), to_dev(g, dtype)
+        out = tf if target == "f" else tg
+        dc.conv_hermitian_1d(tf, tg, out=out)
+        assert rel_l2(out.cpu().numpy(), ref) <= tol_for(dtype, 3 * m)
+
+
+@pytest.mark.parametrize("m", [4096, 32768])
+def test_hermitian_1d_paper_closed_form(dc, m):
     k = np.arange(m)
     f, g = np.sqrt(3) * np.exp(1j * k), np.sqrt(5) * np.exp(1j * k)
     H = np.sqrt(15) * (2 * m - 1 - k) * np.exp(1j * k)
