@@ -44,6 +44,7 @@ struct dc_batched_plan {
   // fixed-shape engine
   bool fx = false;
   bool herm = false;   // centered Hermitian rows (internal uniform plans only)
+  bool tern = false;   // one centered Hermitian ternary convolution of length total (internal)
   const struct FxOps* ops = nullptr;
   fx::HostPlan hp;
   fx::Task* d_tasks = nullptr;
@@ -209,11 +210,14 @@ dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
   return DC_OK;
 }
 
-fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work) {
+fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work,
+                   const void* e = nullptr) {
   fx::FxArgs a{};
   a.f = f;
   a.g = g;
   a.h = h;
+  a.e = e;
+  a.tern = p->tern ? 1 : 0;
   a.off = p->d_off;
   a.order = p->d_order;
   a.tasks = p->d_tasks;
@@ -224,16 +228,17 @@ fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void*
   a.scratch = (char*)work + p->cnt_bytes;
   a.tmp = (char*)work + fx_tmp_offset(p);
   a.l1tmp = p->d_l1tmp;
-  a.in_place = (h == f || h == g) ? 1 : 0;
+  a.in_place = (h == f || h == g || (e && h == e)) ? 1 : 0;
   a.herm = p->herm ? 1 : 0;
   a.wait_limit = fx::kWaitLimit;
   for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
   return a;
 }
 
-dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work, cudaStream_t s) {
+dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work, cudaStream_t s,
+                    const void* e = nullptr) {
   DC_CUDA_TRY(cudaMemsetAsync(work, 0, p->cnt_bytes, s));
-  fx::FxArgs a = fx_args(p, f, g, h, work);
+  fx::FxArgs a = fx_args(p, f, g, h, work, e);
   if (p->inst_first.empty()) return p->ops->launch(a, p->grid, p->smem, s);
   // plain mode: each instance's tasks in a launch of their own (the queue
   // counter is reset before each; the dependency counters are distinct)
@@ -805,6 +810,51 @@ dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, dc_batched_plan** out, b
   g_uplans[key] = p;
   *out = p;
   return DC_OK;
+}
+
+namespace {
+std::map<std::tuple<int, int64_t, int>, dc_batched_plan*> g_tplans;   // (device, m, ds)
+}  // namespace
+
+bool fx_ternary_ok(int64_t m, int ds) { return fx_uniform_ok(2 * m, ds) && fx_uniform_two_level(2 * m); }
+
+size_t fx_ternary_work(int64_t m, int ds) { return fx_uniform_work(1, 2 * m, ds); }
+
+// The plan of one ternary convolution of length m on the fixed engine (a
+// one-instance plan of the M = 2m point sub-transforms whose inputs and
+// output hold m elements), cached per device and precision.
+dc_status fx_ternary_plan(int64_t m, int ds, dc_batched_plan** out) {
+  if (!fx_ternary_ok(m, ds)) return DC_ERR_SIZE;
+  int dev = 0;
+  DC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_umu);
+  auto key = std::make_tuple(dev, m, ds);
+  auto it = g_tplans.find(key);
+  if (it != g_tplans.end()) { *out = it->second; return DC_OK; }
+  std::vector<int64_t> ms(1, 2 * m), off{0, m};
+  dc_batched_plan* p = new dc_batched_plan();
+  p->dtype = ds == 8 ? DC_C64 : DC_C128;
+  p->ds = ds;
+  p->n = 1;
+  p->total = m;
+  p->m_host = ms;
+  p->off_host = off;
+  p->device = dev;
+  p->tern = true;
+  dc_status st = create_fixed(p, ms.data(), 1, off, 0, false);
+  if (st != DC_OK) { dc_batched_plan_destroy(p); return st; }
+  g_tplans[key] = p;
+  *out = p;
+  return DC_OK;
+}
+
+dc_status fx_ternary_run(int64_t m, int ds, const void* f, const void* g, const void* e, void* h, void* work,
+                         size_t work_bytes, cudaStream_t s) {
+  dc_batched_plan* p = nullptr;
+  dc_status st = fx_ternary_plan(m, ds, &p);
+  if (st != DC_OK) return st;
+  if (work_bytes < p->work) return DC_ERR_NOMEM;
+  return fx_launch(p, f, g, h, work, s, e);
 }
 
 }  // namespace dc

@@ -116,6 +116,16 @@ dc_status plan_1d(int kind, int64_t m, int ds, bool with_table, CfgDev* cfg, siz
       if (st != DC_OK) return st;
     }
   }
+  // likewise a ternary convolution whose 2m-point sub-transforms are a
+  // two-level size
+  if (kind == K_TERNARY && fx_ternary_ok(m, ds)) {
+    *work = std::max(*work, fx_ternary_work(m, ds));
+    if (with_table) {
+      dc_batched_plan* p = nullptr;
+      dc_status st = fx_ternary_plan(m, ds, &p);
+      if (st != DC_OK) return st;
+    }
+  }
   return DC_OK;
 }
 
@@ -136,6 +146,8 @@ dc_status run_1d(int kind, const void* const* ins, int nin, void* const* outs, i
     if ((st = fx_uniform_plan(1, m, ds, &p, kind == K_HERMITIAN)) != DC_OK) return st;
     return dc_conv_complex_1d_batched(p, ins[0], ins[1], outs[0], work, work_bytes, s);
   }
+  if (kind == K_TERNARY && fx_ternary_ok(m, ds))
+    return fx_ternary_run(m, ds, ins[0], ins[1], ins[2], outs[0], work, work_bytes, s);
   ConvArgs a{};
   for (int x = 0; x < nin; ++x) a.in[x] = ins[x];
   for (int o = 0; o < nout; ++o) a.out[o] = outs[o];

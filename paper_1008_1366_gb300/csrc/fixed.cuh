@@ -388,9 +388,15 @@ __device__ __forceinline__ void one_middle(C* v, int i, bool act, const Lay& A, 
   }
 }
 
-template <int L, int E, int TN, class Ld, class St, class Sy>
+// pointwise product of the two transformed arrays (binary complex case)
+struct CProd {
+  __device__ __forceinline__ C operator()(C a, C b) const { return cmul(a, b); }
+};
+
+template <int L, int E, int TN, class Ld, class St, class Sy, class Pr = CProd>
 __device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, const Roots<C>& rt,
-                                             const Ld& ld, const St& st, const Sy& sync) {
+                                             const Ld& ld, const St& st, const Sy& sync,
+                                             const Pr& prod = Pr{}) {
   using F = Fft<L, E>;
   constexpr int n = F::n;
   static_assert(n >= 2, "at least two stages");
@@ -427,7 +433,7 @@ __device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, cons
     for (int b = 0; b < K::NB; ++b)
 #pragma unroll
       for (int q = 0; q < K::R; ++q)
-        v[b * K::R + q] = cmul(A[pos<L, E, n - 1, false>(i, b, q)], v[b * K::R + q]);
+        v[b * K::R + q] = prod(A[pos<L, E, n - 1, false>(i, b, q)], v[b * K::R + q]);
     // first forward stage: same radix and positions, no twiddles
     dft<L, E, 0, true, TN>(v, i, rt);
   }

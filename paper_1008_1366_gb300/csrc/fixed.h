@@ -40,6 +40,7 @@ struct FxArgs {
   const void* f;
   const void* g;
   void* h;
+  const void* e;           // third input of ternary convolutions
   const int64_t* off;      // per-instance element offsets
   const int32_t* order;    // instance ids of the level-1 tasks
   const Task* tasks;
@@ -53,6 +54,9 @@ struct FxArgs {
   const int64_t* l1tmp;    // tmp + l1tmp[instance]; others keep them in h
   int32_t in_place;        // h is f or g
   int32_t herm;            // 1: centered Hermitian convolutions, tables of zeta_{3m}
+  int32_t tern;            // 1: centered Hermitian ternary convolutions of length m = M / 2
+                           //    on the M-point sub-transforms (two-level M only)
+  int32_t pad2;
   long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
   const void* tab[kNumSizes];     // root tables zeta_{2m}^i, i < 2m, per size code
 };

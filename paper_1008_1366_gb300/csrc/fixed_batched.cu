@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 #include <vector>
 
 #include "fixed.cuh"
@@ -305,8 +306,97 @@ __device__ __noinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, Root
   }
 }
 
-// pass B: row group `unit` (rows (r, j2), r = row / L2) of level-2 instance l
+// pass A of a centered Hermitian ternary convolution (Sec. 4.2, N = 4m) on
+// the M = 2m point sub-transforms: column tile `tile` of level-2 instance
+// l.  Residue r = 0, 1 transforms V_k = zeta_{4m}^{rk} U_k (k < m, U_0 real),
+// V_m = 0, V_k = conj V_{2m-k} (k > m), of f + i g (first array) and of e
+// (second).  With B_k = U_k (k < m), conj U_{2m-k} (k > m), V_k equals
+// zeta_{4m}^{rk} B_k times (-1)^r above m, since zeta_{4m}^{2m} = -1; the
+// residue-1 factor below carries that sign.
 template <int M>
+__device__ __noinline__ void run_A_tern(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
+  using S = Shape<M>;
+  constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 2 * M, MH = M / 2;
+  using K = Stage<L2, E, 0, false>;
+  const int c = threadIdx.x % W, i = threadIdx.x / W;
+  const int k1 = tile * W + c;
+  const L2Inst in = a->l2[l];
+  C* scr = (C*)a->scratch + in.scr;
+  C tw[E];
+#pragma unroll
+  for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+    for (int q = 0; q < K::R; ++q) {
+      const int k = k1 + L1 * pos<L2, E, 0, false>(i, b, q);
+      C t = rt.at(k);
+      if (k > MH) {
+        t.x = -t.x;
+        t.y = -t.y;
+      }
+      tw[b * K::R + q] = t;
+    }
+#pragma unroll 1
+  for (int arr = 0; arr < 2; ++arr) {
+    const C* u = (const C*)(arr ? a->e : a->f) + in.off;
+    const C* ug = (const C*)a->g + in.off;
+    C raw[E];
+#pragma unroll
+    for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+      for (int q = 0; q < K::R; ++q) {
+        const int k = k1 + L1 * pos<L2, E, 0, false>(i, b, q);
+        const bool up = k > MH;
+        const int kk = k < MH ? k : (up ? M - k : 0);
+        C x = __ldg(u + kk);
+        C y;   // B_k of the second array packed as the imaginary part
+        if (arr == 0) {
+          const C gv = __ldg(ug + kk);
+          if (k == 0) {
+            y.x = x.x;
+            y.y = gv.x;
+          } else if (up) {   // conj f + i conj g
+            y.x = x.x + gv.y;
+            y.y = gv.x - x.y;
+          } else {           // f + i g
+            y.x = x.x - gv.y;
+            y.y = x.y + gv.x;
+          }
+        } else {
+          y.x = x.x;
+          y.y = k == 0 ? (Real)0 : (up ? -x.y : x.y);
+        }
+        if (k == MH) {
+          y.x = 0;
+          y.y = 0;
+        }
+        raw[b * K::R + q] = y;
+      }
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+      C v[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = r ? cmul(raw[e], tw[e]) : raw[e];
+      C* dst = scr + (size_t)(2 * r + arr) * M + k1;
+      column<L2, E, W, TN, false>(v, i, sm + c, rt, [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
+      __syncthreads();
+    }
+  }
+}
+
+// Ternary product (Sec. 4.2): the first array holds u^f + i u^g, the second
+// u^e (both real), their triple product is real.
+struct TernProd {
+  __device__ __forceinline__ C operator()(C a, C b) const {
+    C p;
+    p.x = a.x * a.y * b.x;
+    p.y = 0;
+    return p;
+  }
+};
+
+// pass B: row group `unit` (rows (r, j2), r = row / L2) of level-2 instance
+// l; TERN: the ternary product of a ternary convolution's sub-transforms
+template <int M, bool TERN>
 __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Roots<C> rt) {
   using S = Shape<M>;
   constexpr int L1 = S::L1, L2 = S::L2, E1 = S::E1, T1 = S::T1, GR = S::GR, PL = padded(L1),
@@ -330,14 +420,16 @@ __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Root
         if (arr == 0) tw[e] = rt.at(2 * j2 * x);
         return cmul(__ldcg((arr ? sg : (const C*)sf) + x), tw[e]);
       },
-      [&](int x, int e, C v) { __stcg(sf + x, cmulc(v, tw[e])); }, sync);
+      [&](int x, int e, C v) { __stcg(sf + x, cmulc(v, tw[e])); }, sync,
+      typename std::conditional<TERN, TernProd, CProd>::type{});
   // the g row was read for the last time (every thread of the group loaded
   // its part before the group's first barrier)
   for (int ln = i; ln < L1 * (int)sizeof(C) / 128; ln += T1) discard_l2((const char*)sg + ln * 128);
 }
 
-// pass C: column tile `tile` of level-2 instance l, both residues, output
-template <int M>
+// pass C: column tile `tile` of level-2 instance l, both residues, output;
+// TERN: only the outputs k < M / 2 (a ternary convolution's length)
+template <int M, bool TERN>
 __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
   using S = Shape<M>;
   constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 2 * M;
@@ -362,7 +454,7 @@ __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Root
   __syncthreads();
   column<L2, E, W, TN, true>(vin[1], i, sm + c, rt, [&](int k2, int e, C y) {
     const int k = k1 + L1 * k2;
-    h[(size_t)L1 * k2] = cscale(cadd(y0[e], cmulc(y, rt.at(k))), sc);
+    if (!TERN || 2 * k2 < L2) h[(size_t)L1 * k2] = cscale(cadd(y0[e], cmulc(y, rt.at(k))), sc);
   });
   // both residues' product columns of the tile were read for the last time
   __syncthreads();
@@ -501,30 +593,41 @@ __device__ __noinline__ void run_C_herm(const FxArgs* a, int l, int tile, C* sm,
   }
 }
 
-template <int M>
+// One kernel per kind of convolution, so that each kernel's call graph (and
+// the registers ptxas gives its functions) holds only its own passes.
+enum : int { MODE_COMPLEX = 0, MODE_HERM = 1, MODE_TERN = 2 };
+
+template <int M, int MODE>
 __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C* sm, Roots<C> rt) {
   if constexpr (Shape<M>::l1) {
-    if (a->herm) {
+    if constexpr (MODE == MODE_HERM) {
 #pragma unroll 1
       for (int ri = 0; ri < 3; ++ri) {
         l1_herm_residue<M>(a, ri, x, y, sm, rt);
         __syncthreads();
       }
-      return;
+    } else if constexpr (MODE == MODE_COMPLEX) {
+      l1_residue<M, 0>(a, x, y, sm, rt);
+      __syncthreads();
+      l1_residue<M, 1>(a, x, y, sm, rt);
+    } else {
+      // ternary plans hold two-level sizes only
+      if (threadIdx.x == 0) record_error(a->hdr, DC_ERR_DEVICE, M);
     }
-    l1_residue<M, 0>(a, x, y, sm, rt);
-    __syncthreads();
-    l1_residue<M, 1>(a, x, y, sm, rt);
   } else {
-    if (a->herm) {
+    if constexpr (MODE == MODE_HERM) {
       if (type == T_A) run_A_herm<M>(a, x, y, sm, rt);
       else if (type == T_B) run_B_herm<M>(a, x, y, sm, rt);
       else run_C_herm<M>(a, x, y, sm, rt);
-      return;
+    } else if constexpr (MODE == MODE_TERN) {
+      if (type == T_A) run_A_tern<M>(a, x, y, sm, rt);
+      else if (type == T_B) run_B<M, true>(a, x, y, sm, rt);
+      else run_C<M, true>(a, x, y, sm, rt);
+    } else {
+      if (type == T_A) run_A<M>(a, x, y, sm, rt);
+      else if (type == T_B) run_B<M, false>(a, x, y, sm, rt);
+      else run_C<M, false>(a, x, y, sm, rt);
     }
-    if (type == T_A) run_A<M>(a, x, y, sm, rt);
-    else if (type == T_B) run_B<M>(a, x, y, sm, rt);
-    else run_C<M>(a, x, y, sm, rt);
   }
 }
 
@@ -564,6 +667,7 @@ __device__ __forceinline__ int roots_off_of(int code, bool herm) {
   }
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid_constant__ FxArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* rts = (C*)smem_raw;
@@ -599,12 +703,12 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
     const int code = t.kc & 255, type = t.kc >> 8;
     if (code != cur) {
       // lo = zeta_TN^b (b < 2^sh), hi = zeta_TN^(a 2^sh), from the full table
-      const int TN = (a.herm ? 3 : 2) * size_of_code(code);
+      const int TN = (MODE == MODE_HERM ? 3 : 2) * size_of_code(code);
       const int sh = roots_sh(TN), nlo = 1 << sh, cnt = roots_count(TN);
       const C* tab = (const C*)a.tab[code];
       // the low table always starts shared memory; the high one follows it,
       // or sits behind the task data for the Hermitian level-2 sizes
-      const int hoff = roots_off_of(code, a.herm != 0);
+      const int hoff = roots_off_of(code, MODE == MODE_HERM);
       C* hi = hoff ? (C*)(smem_raw + hoff) : rts + nlo;
       for (int e = threadIdx.x; e < cnt; e += kThreads)
         (e < nlo ? rts[e] : hi[e - nlo]) = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
@@ -615,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
     const long long t_start = clock64();
     switch (code) {
 #define DC_FX_CASE(c) \
-      case c: run_size<size_of_code(c)>(&a, type, t.a, t.b, sm, rt); break;
+      case c: run_size<size_of_code(c), MODE>(&a, type, t.a, t.b, sm, rt); break;
       DC_FX_CASE(0) DC_FX_CASE(1) DC_FX_CASE(2) DC_FX_CASE(3) DC_FX_CASE(4) DC_FX_CASE(5)
       DC_FX_CASE(6) DC_FX_CASE(7) DC_FX_CASE(8) DC_FX_CASE(9) DC_FX_CASE(10)
       DC_FX_CASE(11) DC_FX_CASE(12) DC_FX_CASE(13) DC_FX_CASE(14) DC_FX_CASE(15)
@@ -824,16 +928,22 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
 }
 
 dc_status prepare_kernel(int smem, int* blocks_per_sm) {
-  DC_CUDA_TRY(cudaFuncSetAttribute(fx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  int b = 0;
-  DC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fx_kernel, kThreads, smem));
-  if (b < 1) return DC_ERR_SIZE;
-  *blocks_per_sm = b;
+  int bmin = 1 << 20;
+  for (auto k : {fx_kernel<MODE_COMPLEX>, fx_kernel<MODE_HERM>, fx_kernel<MODE_TERN>}) {
+    DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int b = 0;
+    DC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kThreads, smem));
+    bmin = std::min(bmin, b);
+  }
+  if (bmin < 1) return DC_ERR_SIZE;
+  *blocks_per_sm = bmin;
   return DC_OK;
 }
 
 dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s) {
-  fx_kernel<<<grid, kThreads, smem, s>>>(a);
+  if (a.herm) fx_kernel<MODE_HERM><<<grid, kThreads, smem, s>>>(a);
+  else if (a.tern) fx_kernel<MODE_TERN><<<grid, kThreads, smem, s>>>(a);
+  else fx_kernel<MODE_COMPLEX><<<grid, kThreads, smem, s>>>(a);
   DC_CUDA_TRY(cudaGetLastError());
   return DC_OK;
 }

@@ -32,6 +32,13 @@ bool fx_uniform_two_level(int64_t m);   // m runs as row/column passes spread ov
 size_t fx_uniform_work(int64_t n, int64_t m, int ds);
 // herm: centered Hermitian convolutions (level-1 sizes only)
 dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, struct dc_batched_plan** out, bool herm = false);
+// one centered Hermitian ternary convolution of length m on the fixed engine
+// (2m a two-level size of the set)
+bool fx_ternary_ok(int64_t m, int ds);
+size_t fx_ternary_work(int64_t m, int ds);
+dc_status fx_ternary_plan(int64_t m, int ds, struct dc_batched_plan** out);
+dc_status fx_ternary_run(int64_t m, int ds, const void* f, const void* g, const void* e, void* h, void* work,
+                         size_t work_bytes, cudaStream_t s);
 dc_status conv1d_blocks_per_sm(int kind, int dsize, int smem, int* out);
 
 }  // namespace dc

@@ -112,7 +112,10 @@ def test_hermitian_1d_paper_closed_form(dc, m):
     assert rel_l2(h, H) <= 1e-13
 
 
-TERN = [1, 2, 3, 4, 5, 8, 12, 16, 20, 64, 96, 160, 1024, 2048, 4096, 5120, 16384]
+# 4096 and up with 2m in the size set: the fixed-shape engine's two-level
+# passes over the 2m-point sub-transforms
+TERN = [1, 2, 3, 4, 5, 8, 12, 16, 20, 64, 96, 160, 1024, 2048, 4096, 5120, 6144, 8192, 10240, 12288, 16384,
+        20480, 24576, 32768]
 
 
 @pytest.mark.parametrize("m", TERN)
@@ -122,6 +125,21 @@ def test_ternary_1d(dc, m, dtype):
     ref = oracle.conv_ternary_hermitian(f, g, e)
     h = dc.conv_ternary_hermitian_1d(to_dev(f, dtype), to_dev(g, dtype), to_dev(e, dtype)).cpu().numpy()
     assert rel_l2(h, ref) <= tol_for(dtype, 4 * m)
+
+
+@pytest.mark.parametrize("m", [160, 16384])
+def test_ternary_1d_projection_and_in_place(dc, m):
+    # raw inputs (non-real U_0 projected to its real part, like the oracle);
+    # the output may be any of the three inputs
+    f, g, e = (synthetic.uniform_complex(m, s) for s in (41, 42, 43))
+    ref = oracle.conv_ternary_hermitian(f, g, e)
+    dtype = torch.complex128
+    assert rel_l2(dc.conv_ternary_hermitian_1d(to_dev(f, dtype), to_dev(g, dtype), to_dev(e, dtype)).cpu().numpy(),
+                  ref) <= FP64_TOL
+    for target in range(3):
+        ts = [to_dev(x, dtype) for x in (f, g, e)]
+        dc.conv_ternary_hermitian_1d(*ts, out=ts[target])
+        assert rel_l2(ts[target].cpu().numpy(), ref) <= FP64_TOL
 
 
 @pytest.mark.parametrize("m", [1, 3, 16, 80, 1024, 12288, 32768])
