@@ -126,8 +126,8 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   if (ndim == 3) off += align_up((size_t)md->narr * md->qa * md->S * my * mlast * ds, 256);
   md->off_rows = off;
   size_t rows_bytes = (size_t)md->rows_grid * md->rows_slot;
-  // binary complex rows of a size in the set, and centered Hermitian rows
-  // of a one-level size, run on the fixed-shape engine
+  // binary complex and centered Hermitian rows of a size in the set run on
+  // the fixed-shape engine
   md->rows_n[0] = nrows;
   md->rows_n[1] = ndim == 3 && md->slabs % md->S ? md->qa * (md->slabs % md->S) * my : nrows;
   // Hermitian rows only; the gradient pair (K_HERMITIAN_PAIR) stays on the
@@ -136,7 +136,7 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   // plain convolutions (W + i g) would carry it into g's channel
   const bool herm_rows = md->row_kind == K_HERMITIAN;
   md->rows_fx = (md->row_kind == K_COMPLEX && fx_uniform_ok(mlast, ds)) ||
-                (herm_rows && fx_uniform_ok(mlast, ds) && !fx_uniform_two_level(mlast));
+                (herm_rows && fx_uniform_ok(mlast, ds));
   if (md->rows_fx) {
     rows_bytes = std::max(fx_uniform_work(md->rows_n[0], mlast, ds), fx_uniform_work(md->rows_n[1], mlast, ds));
     // gradient pairs: one temporary array of rows for the second output

@@ -59,7 +59,8 @@ def test_hermitian_nd(dc, ms, dtype):
 
 # wide rows: the row convolutions run on the fixed-shape engine (every
 # size family, both precisions)
-HW = [(2, 64), (2, 80), (3, 96), (2, 640), (2, 1536), (2, 4096), (2, 6144), (4, 5120), (2, 3, 256)]
+HW = [(2, 64), (2, 80), (3, 96), (2, 640), (2, 1536), (2, 4096), (2, 6144), (4, 5120), (2, 3, 256), (2, 8192),
+      (3, 12288), (2, 20480), (2, 2, 16384)]
 
 
 @pytest.mark.parametrize("ms", HW)
