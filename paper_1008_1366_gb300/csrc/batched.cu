@@ -43,8 +43,7 @@ struct dc_batched_plan {
   size_t slot = 0, work = 0;
   // fixed-shape engine
   bool fx = false;
-  bool herm = false;   // centered Hermitian rows (internal uniform plans only)
-  bool tern = false;   // one centered Hermitian ternary convolution of length total (internal)
+  int mode = fx::MODE_COMPLEX;   // kind of convolution (fx::MODE_*; others internal plans only)
   const struct FxOps* ops = nullptr;
   fx::HostPlan hp;
   fx::Task* d_tasks = nullptr;
@@ -74,7 +73,7 @@ struct FxOps {
   int64_t (*code_size)(int);
   void (*code_shape)(int, int*, int*, int*, int*, int*);
   int (*code_smem)(int);
-  bool (*build_plan)(const int64_t*, int32_t, const int64_t*, const fx::Schedule&, bool, fx::HostPlan*);
+  bool (*build_plan)(const int64_t*, int32_t, const int64_t*, const fx::Schedule&, int, fx::HostPlan*);
   dc_status (*prepare_kernel)(int, int*);
   dc_status (*launch)(const fx::FxArgs&, int, int, cudaStream_t);
 };
@@ -211,13 +210,14 @@ dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
 }
 
 fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work,
-                   const void* e = nullptr) {
+                   const void* e = nullptr, void* h2 = nullptr) {
   fx::FxArgs a{};
   a.f = f;
   a.g = g;
   a.h = h;
   a.e = e;
-  a.tern = p->tern ? 1 : 0;
+  a.h2 = h2;
+  a.mode = p->mode;
   a.off = p->d_off;
   a.order = p->d_order;
   a.tasks = p->d_tasks;
@@ -228,17 +228,17 @@ fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void*
   a.scratch = (char*)work + p->cnt_bytes;
   a.tmp = (char*)work + fx_tmp_offset(p);
   a.l1tmp = p->d_l1tmp;
-  a.in_place = (h == f || h == g || (e && h == e)) ? 1 : 0;
-  a.herm = p->herm ? 1 : 0;
+  auto aliases = [&](const void* o) { return o && (o == f || o == g || o == e); };
+  a.in_place = (aliases(h) || aliases(h2)) ? 1 : 0;
   a.wait_limit = fx::kWaitLimit;
   for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
   return a;
 }
 
 dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work, cudaStream_t s,
-                    const void* e = nullptr) {
+                    const void* e = nullptr, void* h2 = nullptr) {
   DC_CUDA_TRY(cudaMemsetAsync(work, 0, p->cnt_bytes, s));
-  fx::FxArgs a = fx_args(p, f, g, h, work, e);
+  fx::FxArgs a = fx_args(p, f, g, h, work, e, h2);
   if (p->inst_first.empty()) return p->ops->launch(a, p->grid, p->smem, s);
   // plain mode: each instance's tasks in a launch of their own (the queue
   // counter is reset before each; the dependency counters are distinct)
@@ -294,7 +294,7 @@ bool fx_build_plain(dc_batched_plan* p, const int64_t* m, int32_t n, const std::
   const fx::Schedule sc{p->grid / 2, 0};
   for (int32_t i = 0; i < n; ++i) {
     fx::HostPlan one;
-    if (!p->ops->build_plan(m + i, 1, off.data() + i, sc, p->herm, &one)) return false;
+    if (!p->ops->build_plan(m + i, 1, off.data() + i, sc, p->mode, &one)) return false;
     const int32_t ob = (int32_t)all.order.size(), lb = (int32_t)all.l2.size(), cb = (int32_t)all.ncnt;
     p->inst_first.push_back((int32_t)all.tasks.size());
     p->inst_count.push_back((int32_t)one.tasks.size());
@@ -321,9 +321,9 @@ bool fx_build_plain(dc_batched_plan* p, const int64_t* m, int32_t n, const std::
 }
 
 dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const std::vector<int64_t>& off,
-                       int32_t flags, bool herm = false) {
+                       int32_t flags, int mode = fx::MODE_COMPLEX) {
   p->fx = true;
-  p->herm = herm;
+  p->mode = mode;
   p->ops = p->ds == 8 ? &kFx32 : &kFx64;
   p->off_host = off;
   int bps = 0;
@@ -335,12 +335,12 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
   p->grid = bps * device_info().sms;
   const fx::Schedule dflt{p->grid / 2, 0};
   const bool plain = (flags & DC_PLAN_ONE_PER_LAUNCH) != 0;
-  if (plain ? !fx_build_plain(p, m, n, off) : !p->ops->build_plan(m, n, off.data(), dflt, p->herm, &p->hp))
+  if (plain ? !fx_build_plain(p, m, n, off) : !p->ops->build_plan(m, n, off.data(), dflt, p->mode, &p->hp))
     return DC_ERR_SIZE;
   p->smem = p->hp.smem;
   for (int c : p->hp.codes) {
     const void* tw = nullptr;
-    st = get_root_table((herm ? 3 : 2) * p->ops->code_size(c), p->ds, &tw);
+    st = get_root_table((fx::mode_tables_3m(mode) ? 3 : 2) * p->ops->code_size(c), p->ds, &tw);
     if (st != DC_OK) return st;
     p->tabs[c] = tw;
   }
@@ -358,14 +358,14 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
       for (int mode = 0; mode < fx::kL1Modes; ++mode) {
         const fx::Schedule sc{cand, mode};
         if (cand < 1 || (cand == dflt.batch_target && mode == dflt.l1_mode)) continue;
-        if (!p->ops->build_plan(m, n, off.data(), sc, p->herm, &p->hp) || fx_upload(p, off) != DC_OK) continue;
+        if (!p->ops->build_plan(m, n, off.data(), sc, p->mode, &p->hp) || fx_upload(p, off) != DC_OK) continue;
         const float t = fx_time(p, s);
         if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; best = sc; }
       }
     }
     cudaStreamDestroy(s);
     cudaGetLastError();
-    if (!p->ops->build_plan(m, n, off.data(), best, p->herm, &p->hp)) return DC_ERR_SIZE;
+    if (!p->ops->build_plan(m, n, off.data(), best, p->mode, &p->hp)) return DC_ERR_SIZE;
     st = fx_upload(p, off);
     if (st != DC_OK) return st;
     p->fx_sched = best;
@@ -569,7 +569,7 @@ dc_status dc_batched_plan_set_schedule(dc_batched_plan* p, int32_t batch_target,
   std::vector<int64_t> ms(p->n);
   for (int32_t i = 0; i < p->n; ++i) ms[i] = p->off_host[i + 1] - p->off_host[i];
   const fx::Schedule sc{batch_target, l1_mode};
-  if (!p->ops->build_plan(ms.data(), p->n, p->off_host.data(), sc, p->herm, &p->hp)) return DC_ERR_SIZE;
+  if (!p->ops->build_plan(ms.data(), p->n, p->off_host.data(), sc, p->mode, &p->hp)) return DC_ERR_SIZE;
   dc_status st = fx_upload(p, p->off_host);
   if (st != DC_OK) return st;
   p->fx_sched = sc;
@@ -731,7 +731,7 @@ dc_status dc_batched_plan_destroy(dc_batched_plan* p) {
 namespace dc {
 namespace {
 std::mutex g_umu;
-std::map<std::tuple<int, int64_t, int64_t, int, bool>, dc_batched_plan*> g_uplans;
+std::map<std::tuple<int, int64_t, int64_t, int, int>, dc_batched_plan*> g_uplans;
 }  // namespace
 
 bool fx_uniform_ok(int64_t m, int ds) { return (ds == 8 || ds == 16) && fx::f32::size_code(m) >= 0; }
@@ -745,26 +745,26 @@ bool fx_uniform_two_level(int64_t m) {
 }
 
 namespace {
-std::map<std::tuple<int, int64_t, int64_t, int>, size_t> g_uwork;   // (device, n, m, ds) -> bytes
+std::map<std::tuple<int, int64_t, int64_t, int, int>, size_t> g_uwork;   // (device, n, m, ds, mode) -> bytes
 }  // namespace
 
-size_t fx_uniform_work_uncached(int64_t n, int64_t m, int ds);
+size_t fx_uniform_work_uncached(int64_t n, int64_t m, int ds, int mode);
 
 // cached: the query runs on every multi-D and 1D call
-size_t fx_uniform_work(int64_t n, int64_t m, int ds) {
-  const auto key = std::make_tuple(device_info().device, n, m, ds);
+size_t fx_uniform_work(int64_t n, int64_t m, int ds, int mode) {
+  const auto key = std::make_tuple(device_info().device, n, m, ds, mode);
   {
     std::lock_guard<std::mutex> lock(g_umu);
     auto it = g_uwork.find(key);
     if (it != g_uwork.end()) return it->second;
   }
-  const size_t b = fx_uniform_work_uncached(n, m, ds);
+  const size_t b = fx_uniform_work_uncached(n, m, ds, mode);
   std::lock_guard<std::mutex> lock(g_umu);
   g_uwork[key] = b;
   return b;
 }
 
-size_t fx_uniform_work_uncached(int64_t n, int64_t m, int ds) {
+size_t fx_uniform_work_uncached(int64_t n, int64_t m, int ds, int mode) {
   const FxOps* ops = ds == 8 ? &kFx32 : &kFx64;
   int smem_all = 0;
   for (int c = 0; c < fx::kNumSizes; ++c) smem_all = std::max(smem_all, ops->code_smem(c));
@@ -773,24 +773,22 @@ size_t fx_uniform_work_uncached(int64_t n, int64_t m, int ds) {
   for (int64_t i = 0; i < n; ++i) off[i + 1] = off[i] + m;
   fx::HostPlan hp;
   const fx::Schedule sc{bps * device_info().sms / 2, 0};
-  // the workspace of a centered Hermitian plan is the same (same scratch
-  // regions and counters; only the task count differs)
-  if (!ops->build_plan(ms.data(), (int32_t)n, off.data(), sc, false, &hp)) return 0;
+  if (!ops->build_plan(ms.data(), (int32_t)n, off.data(), sc, mode, &hp)) return 0;
   (void)smem_all;
   return align_up(sizeof(WorkHeader) + hp.ncnt * sizeof(uint32_t), 256) + align_up(hp.scratch * (size_t)ds, 256) +
          hp.l1_elems * (size_t)ds;
 }
 
-dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, dc_batched_plan** out, bool herm) {
+dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, dc_batched_plan** out, int mode) {
   int dev = 0;
   DC_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(g_umu);
-  auto key = std::make_tuple(dev, n, m, ds, herm);
+  auto key = std::make_tuple(dev, n, m, ds, mode);
   auto it = g_uplans.find(key);
   if (it != g_uplans.end()) { *out = it->second; return DC_OK; }
   std::vector<int64_t> ms((size_t)n, m);
   dc_batched_plan* p = nullptr;
-  if (!herm) {
+  if (mode == fx::MODE_COMPLEX) {
     dc_status st = dc_batched_plan_create(ms.data(), (int32_t)n, ds == 8 ? DC_C64 : DC_C128, 0, &p);
     if (st != DC_OK) return st;
   } else {
@@ -804,7 +802,7 @@ dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, dc_batched_plan** out, b
     p->m_host = ms;
     p->off_host = off;
     DC_CUDA_TRY(cudaGetDevice(&p->device));
-    dc_status st = create_fixed(p, ms.data(), (int32_t)n, off, 0, true);
+    dc_status st = create_fixed(p, ms.data(), (int32_t)n, off, 0, mode);
     if (st != DC_OK) { dc_batched_plan_destroy(p); return st; }
   }
   g_uplans[key] = p;
@@ -818,7 +816,7 @@ std::map<std::tuple<int, int64_t, int>, dc_batched_plan*> g_tplans;   // (device
 
 bool fx_ternary_ok(int64_t m, int ds) { return fx_uniform_ok(2 * m, ds) && fx_uniform_two_level(2 * m); }
 
-size_t fx_ternary_work(int64_t m, int ds) { return fx_uniform_work(1, 2 * m, ds); }
+size_t fx_ternary_work(int64_t m, int ds) { return fx_uniform_work(1, 2 * m, ds, fx::MODE_TERN); }
 
 // The plan of one ternary convolution of length m on the fixed engine (a
 // one-instance plan of the M = 2m point sub-transforms whose inputs and
@@ -840,8 +838,7 @@ dc_status fx_ternary_plan(int64_t m, int ds, dc_batched_plan** out) {
   p->m_host = ms;
   p->off_host = off;
   p->device = dev;
-  p->tern = true;
-  dc_status st = create_fixed(p, ms.data(), 1, off, 0, false);
+  dc_status st = create_fixed(p, ms.data(), 1, off, 0, fx::MODE_TERN);
   if (st != DC_OK) { dc_batched_plan_destroy(p); return st; }
   g_tplans[key] = p;
   *out = p;
@@ -855,6 +852,13 @@ dc_status fx_ternary_run(int64_t m, int ds, const void* f, const void* g, const 
   if (st != DC_OK) return st;
   if (work_bytes < p->work) return DC_ERR_NOMEM;
   return fx_launch(p, f, g, h, work, s, e);
+}
+
+dc_status fx_pair_run(dc_batched_plan* p, const void* w, const void* f, const void* g, void* df, void* dg,
+                      void* work, size_t work_bytes, cudaStream_t s) {
+  if (!p || p->mode != fx::MODE_PAIR) return DC_ERR_ARG;
+  if (work_bytes < p->work) return DC_ERR_NOMEM;
+  return fx_launch(p, w, f, df, work, s, g, dg);
 }
 
 }  // namespace dc

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "conv1d.cuh"
+#include "fixed.h"
 #include "launch.h"
 #include "multid.h"
 #include "plan.h"
@@ -89,6 +90,8 @@ dc_status check_work(void* work, size_t have, size_t need) {
   return DC_OK;
 }
 
+int fixed_mode(int kind) { return kind == K_HERMITIAN ? fx::MODE_HERM : fx::MODE_COMPLEX; }
+
 bool on_fixed_engine(int kind, int64_t m, int ds) {
   return (kind == K_COMPLEX || kind == K_HERMITIAN) && fx_uniform_ok(m, ds) && fx_uniform_two_level(m);
 }
@@ -109,10 +112,10 @@ dc_status plan_1d(int kind, int64_t m, int ds, bool with_table, CfgDev* cfg, siz
   // cached): its passes spread over many blocks, where the runtime-shaped
   // kernel gives the instance one
   if (on_fixed_engine(kind, m, ds)) {
-    *work = std::max(*work, fx_uniform_work(1, m, ds));
+    *work = std::max(*work, fx_uniform_work(1, m, ds, fixed_mode(kind)));
     if (with_table) {
       dc_batched_plan* p = nullptr;
-      dc_status st = fx_uniform_plan(1, m, ds, &p, kind == K_HERMITIAN);
+      dc_status st = fx_uniform_plan(1, m, ds, &p, fixed_mode(kind));
       if (st != DC_OK) return st;
     }
   }
@@ -143,7 +146,7 @@ dc_status run_1d(int kind, const void* const* ins, int nin, void* const* outs, i
   cudaStream_t s = (cudaStream_t)stream;
   if (on_fixed_engine(kind, m, ds)) {
     dc_batched_plan* p = nullptr;
-    if ((st = fx_uniform_plan(1, m, ds, &p, kind == K_HERMITIAN)) != DC_OK) return st;
+    if ((st = fx_uniform_plan(1, m, ds, &p, fixed_mode(kind))) != DC_OK) return st;
     return dc_conv_complex_1d_batched(p, ins[0], ins[1], outs[0], work, work_bytes, s);
   }
   if (kind == K_TERNARY && fx_ternary_ok(m, ds))

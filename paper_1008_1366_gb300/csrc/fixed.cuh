@@ -503,6 +503,78 @@ __device__ __forceinline__ void conv1_residue(int i, C* Ap, const Roots<C>& rt, 
 }
 
 // ---------------------------------------------------------------------------
+// one residue of the rows of a centered Hermitian gradient (two Hermitian
+// convolutions sharing W, Sec. 2.3 applied to the adjoint): array A takes
+// W's packed input (its transform is real; the real part is kept), array B
+// w^f + i w^g.  The real products u^W u^g (output 0) and u^W u^f (output 1)
+// take one forward transform each; the second waits in B at the positions
+// where it was formed.  ld(x, arr, e) gives input arr at natural index x;
+// st(x, e, v, o) takes output o.
+// ---------------------------------------------------------------------------
+template <int L, int E, int TN, class Ld, class St, class Sy>
+__device__ __forceinline__ void conv_pair_residue(int i, C* Ap, C* Bp, const Roots<C>& rt, const Ld& ld,
+                                                  const St& st, const Sy& sync) {
+  using F = Fft<L, E>;
+  constexpr int n = F::n;
+  static_assert(n >= 2, "at least two stages");
+  const Contig A{Ap}, B{Bp};
+  C v[E];
+#pragma unroll
+  for (int arr = 0; arr < 2; ++arr) {
+    using K = Stage<L, E, 0, false>;
+#pragma unroll
+    for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+      for (int q = 0; q < K::R; ++q) v[b * K::R + q] = ld(pos<L, E, 0, false>(i, b, q), arr, b * K::R + q);
+    dft<L, E, 0, false, TN>(v, i, rt);
+    scatter<L, E, 0, false>(v, i, arr ? B : A);
+  }
+  sync();
+  bwd_middle<L, E, TN, 1>(v, i, true, A, B, rt, sync);
+  gather<L, E, n - 1, false>(v, i, A);
+  dft<L, E, n - 1, false, TN>(v, i, rt);
+  scatter<L, E, n - 1, false>(v, i, A);
+  if constexpr (n > 2) sync();
+  gather<L, E, n - 1, false>(v, i, B);
+  dft<L, E, n - 1, false, TN>(v, i, rt);
+  using KB = Stage<L, E, n - 1, false>;
+#pragma unroll
+  for (int b = 0; b < KB::NB; ++b)
+#pragma unroll
+    for (int q = 0; q < KB::R; ++q) {
+      const int x = pos<L, E, n - 1, false>(i, b, q), e = b * KB::R + q;
+      const Real uw = A[x].x;
+      C p1;
+      p1.x = uw * v[e].x;
+      p1.y = 0;
+      B[x] = p1;
+      v[e].x = uw * v[e].y;
+      v[e].y = 0;
+    }
+  using KF = Stage<L, E, n - 1, true>;
+#pragma unroll 1
+  for (int o = 0; o < 2; ++o) {
+    if (o == 1) {
+#pragma unroll
+      for (int b = 0; b < KB::NB; ++b)
+#pragma unroll
+        for (int q = 0; q < KB::R; ++q) v[b * KB::R + q] = B[pos<L, E, n - 1, false>(i, b, q)];
+    }
+    dft<L, E, 0, true, TN>(v, i, rt);
+    sync();
+    scatter<L, E, 0, true>(v, i, A);
+    sync();
+    one_middle<L, E, TN, true, 1>(v, i, true, A, rt, sync);
+    gather<L, E, n - 1, true>(v, i, A);
+    dft<L, E, n - 1, true, TN>(v, i, rt);
+#pragma unroll
+    for (int b = 0; b < KF::NB; ++b)
+#pragma unroll
+      for (int q = 0; q < KF::R; ++q) st(pos<L, E, n - 1, true>(i, b, q), b * KF::R + q, v[b * KF::R + q], o);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // one L-point column transform of a tile (passes A and C).  v holds the
 // inputs of stage 0 in gather order; st(x, e, v) takes output x (register e).  D: this
 // thread's column of the interleaved tile.  Every thread calls this.

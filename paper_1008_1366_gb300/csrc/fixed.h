@@ -18,6 +18,17 @@ constexpr int kNumSizes = 31;   // {2^a, 3*2^a, 5*2^a} in [64, 65536]
 // task types of the persistent queue
 enum : int32_t { T_L1 = 0, T_A = 1, T_B = 2, T_C = 3 };
 
+// kind of convolution a plan runs (one kernel instantiation each)
+//   MODE_COMPLEX  binary complex (N = 2m), both levels
+//   MODE_HERM     centered Hermitian (N = 3m), both levels, tables of zeta_{3m}
+//   MODE_TERN     centered Hermitian ternary of length m = M / 2 on the
+//                 M-point sub-transforms (N = 4m), two-level M only
+//   MODE_PAIR     rows of a centered Hermitian gradient: inputs (W, f, g) in
+//                 (f, g, e), outputs conv(W, g) in h and conv(W, f) in h2,
+//                 tables of zeta_{3m}, one-level sizes only
+enum : int32_t { MODE_COMPLEX = 0, MODE_HERM = 1, MODE_TERN = 2, MODE_PAIR = 3 };
+__host__ __device__ constexpr bool mode_tables_3m(int mode) { return mode == MODE_HERM || mode == MODE_PAIR; }
+
 // One queue entry.  kc = type << 8 | size code.  T_L1: a = first slot of
 // the order array, b = instance count.  T_A/T_B/T_C: a = level-2 instance,
 // b = column tile (A, C) or row group (B).  Before it starts the task waits
@@ -40,7 +51,8 @@ struct FxArgs {
   const void* f;
   const void* g;
   void* h;
-  const void* e;           // third input of ternary convolutions
+  const void* e;           // third input (ternary: e; gradient pair: g)
+  void* h2;                // second output (gradient pair)
   const int64_t* off;      // per-instance element offsets
   const int32_t* order;    // instance ids of the level-1 tasks
   const Task* tasks;
@@ -52,11 +64,8 @@ struct FxArgs {
   void* scratch;
   void* tmp;               // level-1 partial outputs (residue 0) of in-place calls,
   const int64_t* l1tmp;    // tmp + l1tmp[instance]; others keep them in h
-  int32_t in_place;        // h is f or g
-  int32_t herm;            // 1: centered Hermitian convolutions, tables of zeta_{3m}
-  int32_t tern;            // 1: centered Hermitian ternary convolutions of length m = M / 2
-                           //    on the M-point sub-transforms (two-level M only)
-  int32_t pad2;
+  int32_t in_place;        // an output is an input
+  int32_t mode;            // MODE_*
   long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
   const void* tab[kNumSizes];     // root tables zeta_{2m}^i, i < 2m, per size code
 };
@@ -94,10 +103,10 @@ constexpr long long kWaitLimit = 1ll << 32;   // about two seconds at 2 GHz
   void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W);           \
   /* dynamic shared memory the kernel needs for a size code */                              \
   int code_smem(int code);                                                                  \
-  /* the task queue for n instances of sizes m[i] at element offsets off[i]; herm: */     \
-  /* centered Hermitian convolutions (three residues: more row tasks per instance) */       \
+  /* the task queue for n instances of sizes m[i] at element offsets off[i] for a */      \
+  /* convolution kind (MODE_*: row tasks and partial-output slots per instance) */         \
   bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc,     \
-                  bool herm, HostPlan* out);                                                \
+                  int mode, HostPlan* out);                                                 \
   /* kernel attributes, occupancy */                                                        \
   dc_status prepare_kernel(int smem, int* blocks_per_sm);                                   \
   dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s);

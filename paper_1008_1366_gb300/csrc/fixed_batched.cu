@@ -245,6 +245,74 @@ __device__ __noinline__ void l1_herm_residue(const FxArgs* a, int ri, int first,
       sync);
 }
 
+// level 1, rows of a centered Hermitian gradient: residue ri (r = ri - 1)
+// of `count` instances.  Inputs W, f, g (in f, g, e); outputs conv(W, g)
+// (h) and conv(W, f) (h2), each Eq. (2.7) with the residue inputs w_{k,r}
+// of l1_herm_residue.  W is transformed alone and f, g packed.  In-place
+// calls keep both partial outputs in two slots of the workspace.
+template <int M>
+__device__ __noinline__ void l1_pair_residue(const FxArgs* a, int ri, int first, int count, C* sm, Roots<C> rt) {
+  using S = Shape<M>;
+  constexpr int E = S::E, T = S::T, PL = padded(M), GS = group_stride(M, T), TN = 3 * M;
+  const int gi = threadIdx.x / T, i = threadIdx.x % T;
+  const bool act = gi < count;
+  const int64_t off = act ? a->off[a->order[first + gi]] : 0;
+  const C* w = (const C*)a->f + off;
+  const C* f = (const C*)a->g + off;
+  const C* g = (const C*)a->e + off;
+  C* h0 = (C*)a->h + off;
+  C* h1 = (C*)a->h2 + off;
+  C* p0 = a->in_place ? (C*)a->tmp + (act ? a->l1tmp[a->order[first + gi]] : 0) : h0;
+  C* p1 = a->in_place ? p0 + M : h1;
+  C* A = sm + gi * GS;
+  const Real sc = (Real)1 / (Real)(3 * M);
+  const GroupSync<T> sync{1 + gi};
+  const int r = ri - 1;
+  C z3;
+  z3.x = (Real)-0.5;
+  z3.y = (Real)(-r) * (Real)0.86602540378443864676;
+  auto wk = [&](const C* u, int x) {
+    C v;
+    if (x == 0) {
+      v = __ldg(u);
+      v.y = 0;
+      return v;
+    }
+    C p = __ldg(u + x), q = __ldg(u + (M - x));
+    q.y = -q.y;
+    if (r == 0) return cadd(p, q);
+    v = cadd(p, cmul(q, z3));
+    const C t = rt.at(x);
+    return r > 0 ? cmul(v, t) : cmulc(v, t);
+  };
+  conv_pair_residue<M, E, TN>(
+      i, A, A + PL, rt,
+      [&](int x, int arr, int) {
+        C v;
+        v.x = 0;
+        v.y = 0;
+        if (!act) return v;
+        if (arr == 0) return wk(w, x);
+        const C wf = wk(f, x), wg = wk(g, x);
+        v.x = wf.x - wg.y;   // w^f + i w^g
+        v.y = wf.y + wg.x;
+        return v;
+      },
+      [&](int x, int, C v, int o) {
+        if (!act) return;
+        if (r != 0) {
+          const C t = rt.at(x);
+          v = r > 0 ? cmulc(v, t) : cmul(v, t);
+        }
+        v = cscale(v, sc);
+        C* p = o ? p1 : p0;
+        if (ri == 0) p[x] = v;
+        else if (ri == 1) p[x] = cadd(p[x], v);
+        else (o ? h1 : h0)[x] = cadd(p[x], v);
+      },
+      sync);
+}
+
 // pass A: column tile `tile` of level-2 instance l.  Each pass is its own
 // function so that registers are allocated per pass.
 template <int M>
@@ -593,9 +661,9 @@ __device__ __noinline__ void run_C_herm(const FxArgs* a, int l, int tile, C* sm,
   }
 }
 
-// One kernel per kind of convolution, so that each kernel's call graph (and
-// the registers ptxas gives its functions) holds only its own passes.
-enum : int { MODE_COMPLEX = 0, MODE_HERM = 1, MODE_TERN = 2 };
+// One kernel per kind of convolution (MODE_*), so that each kernel's call
+// graph (and the registers ptxas gives its functions) holds only its own
+// passes.
 
 template <int M, int MODE>
 __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C* sm, Roots<C> rt) {
@@ -610,12 +678,21 @@ __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C
       l1_residue<M, 0>(a, x, y, sm, rt);
       __syncthreads();
       l1_residue<M, 1>(a, x, y, sm, rt);
+    } else if constexpr (MODE == MODE_PAIR) {
+#pragma unroll 1
+      for (int ri = 0; ri < 3; ++ri) {
+        l1_pair_residue<M>(a, ri, x, y, sm, rt);
+        __syncthreads();
+      }
     } else {
-      // ternary plans hold two-level sizes only
+      // ternary plans hold two-level sizes only (the planner refuses others)
       if (threadIdx.x == 0) record_error(a->hdr, DC_ERR_DEVICE, M);
     }
   } else {
-    if constexpr (MODE == MODE_HERM) {
+    if constexpr (MODE == MODE_PAIR) {
+      // gradient-pair plans hold one-level sizes only (the planner refuses others)
+      if (threadIdx.x == 0) record_error(a->hdr, DC_ERR_DEVICE, M);
+    } else if constexpr (MODE == MODE_HERM) {
       if (type == T_A) run_A_herm<M>(a, x, y, sm, rt);
       else if (type == T_B) run_B_herm<M>(a, x, y, sm, rt);
       else run_C_herm<M>(a, x, y, sm, rt);
@@ -703,12 +780,12 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
     const int code = t.kc & 255, type = t.kc >> 8;
     if (code != cur) {
       // lo = zeta_TN^b (b < 2^sh), hi = zeta_TN^(a 2^sh), from the full table
-      const int TN = (MODE == MODE_HERM ? 3 : 2) * size_of_code(code);
+      const int TN = (mode_tables_3m(MODE) ? 3 : 2) * size_of_code(code);
       const int sh = roots_sh(TN), nlo = 1 << sh, cnt = roots_count(TN);
       const C* tab = (const C*)a.tab[code];
       // the low table always starts shared memory; the high one follows it,
       // or sits behind the task data for the Hermitian level-2 sizes
-      const int hoff = roots_off_of(code, MODE == MODE_HERM);
+      const int hoff = roots_off_of(code, mode_tables_3m(MODE));
       C* hi = hoff ? (C*)(smem_raw + hoff) : rts + nlo;
       for (int e = threadIdx.x; e < cnt; e += kThreads)
         (e < nlo ? rts[e] : hi[e - nlo]) = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
@@ -786,7 +863,7 @@ void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W) {
   *W = t.lvl[code] == 1 ? 0 : t.w[code];
 }
 
-bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc, bool herm, HostPlan* out) {
+bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc, int mode, HostPlan* out) {
   const int batch_target = std::max(1, sc.batch_target);
   const Tables& tb = tables();
   HostPlan& P = *out;
@@ -798,11 +875,13 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   for (int32_t i = 0; i < n; ++i) {
     const int c = size_code(m[i]);
     if (c < 0) return false;
+    if ((mode == MODE_TERN && tb.lvl[c] == 1) || (mode == MODE_PAIR && tb.lvl[c] == 2)) return false;
     used[c] = true;
     if (tb.lvl[c] == 1) {
       l1_by_code[c].push_back(i);
+      // in-place partial outputs: one slot per output
       P.l1tmp[i] = (int64_t)P.l1_elems;
-      P.l1_elems += (size_t)m[i];
+      P.l1_elems += (size_t)m[i] * (mode == MODE_PAIR ? 2 : 1);
     } else {
       big.push_back({c, i});
     }
@@ -884,7 +963,7 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   auto emit = [&](int type, int k) {
     for (int l : batches[k]) {
       const int c = big[l].first;
-      const int nbc = herm ? tb.nbh[c] : tb.nb[c];
+      const int nbc = mode == MODE_HERM ? tb.nbh[c] : tb.nb[c];
       const int cnt = type == T_B ? nbc : tb.na[c];
       for (int u = 0; u < cnt; ++u) {
         Task t{(type << 8) | c, l, u, -1, 0, -1};
@@ -929,7 +1008,7 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
 
 dc_status prepare_kernel(int smem, int* blocks_per_sm) {
   int bmin = 1 << 20;
-  for (auto k : {fx_kernel<MODE_COMPLEX>, fx_kernel<MODE_HERM>, fx_kernel<MODE_TERN>}) {
+  for (auto k : {fx_kernel<MODE_COMPLEX>, fx_kernel<MODE_HERM>, fx_kernel<MODE_TERN>, fx_kernel<MODE_PAIR>}) {
     DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int b = 0;
     DC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kThreads, smem));
@@ -941,9 +1020,13 @@ dc_status prepare_kernel(int smem, int* blocks_per_sm) {
 }
 
 dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s) {
-  if (a.herm) fx_kernel<MODE_HERM><<<grid, kThreads, smem, s>>>(a);
-  else if (a.tern) fx_kernel<MODE_TERN><<<grid, kThreads, smem, s>>>(a);
-  else fx_kernel<MODE_COMPLEX><<<grid, kThreads, smem, s>>>(a);
+  switch (a.mode) {
+    case MODE_COMPLEX: fx_kernel<MODE_COMPLEX><<<grid, kThreads, smem, s>>>(a); break;
+    case MODE_HERM: fx_kernel<MODE_HERM><<<grid, kThreads, smem, s>>>(a); break;
+    case MODE_TERN: fx_kernel<MODE_TERN><<<grid, kThreads, smem, s>>>(a); break;
+    case MODE_PAIR: fx_kernel<MODE_PAIR><<<grid, kThreads, smem, s>>>(a); break;
+    default: return DC_ERR_ARG;
+  }
   DC_CUDA_TRY(cudaGetLastError());
   return DC_OK;
 }

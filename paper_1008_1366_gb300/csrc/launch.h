@@ -29,9 +29,14 @@ dc_status launch_conv1d(int kind, int dsize, const ConvArgs& a, int grid, int sm
 // the workspace bytes (host-only), and the cached plan (created on first use).
 bool fx_uniform_ok(int64_t m, int ds);
 bool fx_uniform_two_level(int64_t m);   // m runs as row/column passes spread over many blocks
-size_t fx_uniform_work(int64_t n, int64_t m, int ds);
+// mode: the fixed engine's kind of convolution (fx::MODE_*, 0 = binary complex)
+size_t fx_uniform_work(int64_t n, int64_t m, int ds, int mode = 0);
 // herm: centered Hermitian convolutions (level-1 sizes only)
-dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, struct dc_batched_plan** out, bool herm = false);
+dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, struct dc_batched_plan** out, int mode = 0);
+// the rows of a centered Hermitian gradient on a MODE_PAIR plan:
+// df = conv(w, g), dg = conv(w, f); outputs may be inputs
+dc_status fx_pair_run(struct dc_batched_plan* p, const void* w, const void* f, const void* g, void* df, void* dg,
+                      void* work, size_t work_bytes, cudaStream_t s);
 // one centered Hermitian ternary convolution of length m on the fixed engine
 // (2m a two-level size of the set)
 bool fx_ternary_ok(int64_t m, int ds);

@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "conv1d.cuh"
+#include "fixed.h"
 #include "launch.h"
 #include "multid.h"
 #include "plan.h"
@@ -24,6 +25,16 @@
 
 namespace dc {
 namespace {
+
+// the fixed engine's kind for a row kind, -1 where it has none
+int row_mode(int row_kind) {
+  switch (row_kind) {
+    case K_COMPLEX: return fx::MODE_COMPLEX;
+    case K_HERMITIAN: return fx::MODE_HERM;
+    case K_HERMITIAN_PAIR: return fx::MODE_PAIR;
+  }
+  return -1;
+}
 
 constexpr size_t kHeader = sizeof(WorkHeader);
 constexpr size_t kChunkBudget = 64ull << 20;   // bytes of (y, z) work arrays per chunk
@@ -41,9 +52,9 @@ struct Md {
   int64_t S = 0;              // 3D: slabs per chunk
   AxisArgs ax, ay;            // outer-axis templates (plan, tile width, table)
   CfgDev rows;                // row configuration
-  bool rows_fx = false;       // rows on the fixed-shape engine (binary complex, size in the set)
+  bool rows_fx = false;       // rows on the fixed-shape engine
+  int rows_mode = -1;         // its kind of convolution (fx::MODE_*)
   int64_t rows_n[2] = {0, 0}; // row counts of the row launches (full chunk, last chunk)
-  size_t off_pair = 0;        // gradient pairs: the temporary rows, inside the rows region
   int rows_grid = 1;
   size_t rows_slot = 0;
   size_t off_y = 0, off_rows = 0, total = 0;
@@ -126,28 +137,25 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   if (ndim == 3) off += align_up((size_t)md->narr * md->qa * md->S * my * mlast * ds, 256);
   md->off_rows = off;
   size_t rows_bytes = (size_t)md->rows_grid * md->rows_slot;
-  // binary complex and centered Hermitian rows of a size in the set run on
-  // the fixed-shape engine
+  // binary complex and centered Hermitian rows of a size in the set, and
+  // the gradient pair rows of a one-level size, run on the fixed-shape
+  // engine
   md->rows_n[0] = nrows;
   md->rows_n[1] = ndim == 3 && md->slabs % md->S ? md->qa * (md->slabs % md->S) * my : nrows;
-  // Hermitian rows only; the gradient pair (K_HERMITIAN_PAIR) stays on the
-  // runtime-shaped kernel: it transforms W alone and keeps the real part,
-  // which drops any non-Hermitian rounding of W's rows, while two packed
-  // plain convolutions (W + i g) would carry it into g's channel
-  const bool herm_rows = md->row_kind == K_HERMITIAN;
-  md->rows_fx = (md->row_kind == K_COMPLEX && fx_uniform_ok(mlast, ds)) ||
-                (herm_rows && fx_uniform_ok(mlast, ds));
+  // The gradient pair transforms W alone and keeps the real part of its
+  // transform, which drops any non-Hermitian rounding of W's rows (two
+  // plain convolutions with W packed beside g would carry it into g's
+  // channel).
+  md->rows_mode = row_mode(md->row_kind);
+  md->rows_fx = fx_uniform_ok(mlast, ds) && md->rows_mode >= 0 &&
+                (md->rows_mode != fx::MODE_PAIR || !fx_uniform_two_level(mlast));
   if (md->rows_fx) {
-    rows_bytes = std::max(fx_uniform_work(md->rows_n[0], mlast, ds), fx_uniform_work(md->rows_n[1], mlast, ds));
-    // gradient pairs: one temporary array of rows for the second output
-    if (md->row_kind == K_HERMITIAN_PAIR) {
-      md->off_pair = align_up(rows_bytes, 256);
-      rows_bytes = md->off_pair + (size_t)std::max(md->rows_n[0], md->rows_n[1]) * mlast * ds;
-    }
+    rows_bytes = std::max(fx_uniform_work(md->rows_n[0], mlast, ds, md->rows_mode),
+                          fx_uniform_work(md->rows_n[1], mlast, ds, md->rows_mode));
     if (with_tables) {
       for (int k = 0; k < 2; ++k) {
         dc_batched_plan* p = nullptr;
-        dc_status st = fx_uniform_plan(md->rows_n[k], mlast, ds, &p, herm_rows);
+        dc_status st = fx_uniform_plan(md->rows_n[k], mlast, ds, &p, md->rows_mode);
         if (st != DC_OK) return st;
       }
     }
@@ -162,22 +170,13 @@ dc_status run_rows(const Md& md, const void* const* in, void* const* out, int64_
   if (md.rows_fx) {
     // the rows' own status header sits at the start of their region
     const int64_t m = md.m[md.ndim - 1];
-    const bool pair = md.row_kind == K_HERMITIAN_PAIR;
     dc_batched_plan* p = nullptr;
-    dc_status st = fx_uniform_plan(nrows, m, md.ds, &p, md.row_kind != K_COMPLEX);
+    dc_status st = fx_uniform_plan(nrows, m, md.ds, &p, md.rows_mode);
     if (st != DC_OK) return st;
     char* rw = work + md.off_rows;
-    if (!pair) return dc_conv_complex_1d_batched(p, in[0], in[1], out[0], rw, md.total - md.off_rows, s);
-    // gradient rows: dg = conv(W, f) into the temporary, then df = conv(W, g)
-    // over f (no longer read), then dg over g; the same transforms as a
-    // shared-W pair, since each plain convolution packs its two inputs
-    // into one transform
-    const size_t wb = md.off_pair;
-    void* tmp = rw + md.off_pair;
-    if ((st = dc_conv_complex_1d_batched(p, in[0], in[1], tmp, rw, wb, s)) != DC_OK) return st;
-    if ((st = dc_conv_complex_1d_batched(p, in[0], in[2], out[0], rw, wb, s)) != DC_OK) return st;
-    DC_CUDA_TRY(cudaMemcpyAsync(out[1], tmp, (size_t)nrows * m * md.ds, cudaMemcpyDeviceToDevice, s));
-    return DC_OK;
+    const size_t rb = md.total - md.off_rows;
+    if (md.rows_mode == fx::MODE_PAIR) return fx_pair_run(p, in[0], in[1], in[2], out[0], out[1], rw, rb, s);
+    return dc_conv_complex_1d_batched(p, in[0], in[1], out[0], rw, rb, s);
   }
   ConvArgs a{};
   for (int x = 0; x < 3; ++x) a.in[x] = in[x];

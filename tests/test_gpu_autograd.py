@@ -38,7 +38,7 @@ def test_gradcheck_hermitian(ag, ms):
     assert torch.autograd.gradcheck(ag.conv_hermitian, (f, g), eps=1e-6, atol=1e-8, rtol=1e-6)
 
 
-@pytest.mark.parametrize("ms", [(64,), (16, 12), (6, 6, 8)])
+@pytest.mark.parametrize("ms", [(64,), (16, 12), (6, 6, 8), (4, 64), (2, 3, 96)])
 def test_backward_matches_oracle_gradient(ag, ms):
     shape = synthetic.hermitian_shape(ms)
     f0 = synthetic.hermitian_spectrum(shape, 11 / 6, 5)

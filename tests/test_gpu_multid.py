@@ -94,7 +94,10 @@ def test_complex_nd_adjoint(dc, shape, dtype):
     assert rel_l2(dg.cpu().numpy(), rdg) <= tol(dtype, N)
 
 
-@pytest.mark.parametrize("ms", [(3, 4), (8, 8), (2, 3, 4), (4, 4, 6)])
+# last axis 64 and up (one-level sizes of the set): the gradient rows run on
+# the fixed-shape engine's pair residue
+@pytest.mark.parametrize("ms", [(3, 4), (8, 8), (2, 3, 4), (4, 4, 6), (3, 64), (2, 96), (2, 3, 80), (2, 640),
+                                (2, 4096), (2, 2, 256)])
 @pytest.mark.parametrize("dtype", DT)
 def test_hermitian_nd_adjoint(dc, ms, dtype):
     shape = synthetic.hermitian_shape(ms)
