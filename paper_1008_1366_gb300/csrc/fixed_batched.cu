@@ -114,6 +114,59 @@ template <int M> struct Shape {
 // device side
 // ---------------------------------------------------------------------------
 
+// Residue r of a centered Hermitian convolution (Sec. 2.3, N = 3m), in a
+// form without branches on r or k, so that the loads of all E elements of
+// a thread can be issued together.  The packed input of f and g at k is
+// zeta_{3m}^{rk} (P_k + zeta_3^{-r} Q_k) with P_k = f_k + i g_k and
+// Q_k = conj f_{m-k} + i conj g_{m-k} (Eqs. (2.4)-(2.5) with Hermitian
+// symmetry); at k = 0 it is Re f_0 + i Re g_0.  For r = 0 both factors are
+// 1 (the table lookup at index 0).  The output factor is zeta_{3m}^{-rk}
+// (Eq. (2.7)).
+struct HermTerms {
+  int r;
+  C z3;   // zeta_3^{-r}, 1 for r = 0
+  __device__ __forceinline__ explicit HermTerms(int r_) : r(r_) {
+    z3.x = r_ ? (Real)-0.5 : (Real)1;
+    z3.y = (Real)(-r_) * (Real)0.86602540378443864676;
+  }
+  // zeta_{3m}^{s r k}
+  __device__ __forceinline__ C tw(int x, const Roots<C>& rt, int s) const {
+    C t = rt.at(r ? x : 0);
+    if (r * s < 0) t.y = -t.y;
+    return t;
+  }
+  template <int M>
+  __device__ __forceinline__ C packed(const C* f, const C* g, int x, const Roots<C>& rt) const {
+    const int mx = x ? M - x : 0;
+    const C fk = __ldg(f + x), gk = __ldg(g + x), fm = __ldg(f + mx), gm = __ldg(g + mx);
+    C P, Q;
+    P.x = fk.x - gk.y;
+    P.y = fk.y + gk.x;
+    Q.x = fm.x + gm.y;
+    Q.y = gm.x - fm.y;
+    C v = cmul(cadd(P, cmul(Q, z3)), tw(x, rt, 1));
+    if (x == 0) {
+      v.x = fk.x;
+      v.y = gk.x;
+    }
+    return v;
+  }
+  template <int M>
+  __device__ __forceinline__ C single(const C* u, int x, const Roots<C>& rt) const {
+    const int mx = x ? M - x : 0;
+    const C p = __ldg(u + x);
+    C q = __ldg(u + mx);
+    q.y = -q.y;
+    C v = cmul(cadd(p, cmul(q, z3)), tw(x, rt, 1));
+    if (x == 0) {
+      v.x = p.x;
+      v.y = 0;
+    }
+    return v;
+  }
+  __device__ __forceinline__ C out(C v, int x, const Roots<C>& rt) const { return cmul(v, tw(x, rt, -1)); }
+};
+
 // level 1: residue R of `count` instances of size M, one thread group each.
 // One function per residue: inlining both lets the compiler share index
 // arithmetic across them, which costs registers and spills.
@@ -198,49 +251,22 @@ __device__ __noinline__ void l1_herm_residue(const FxArgs* a, int ri, int first,
   C* A = sm + gi * GS;
   const Real sc = (Real)1 / (Real)(3 * M);
   const GroupSync<T> sync{1 + gi};
-  const int r = ri - 1;
-  C z3;
-  z3.x = (Real)-0.5;
-  z3.y = (Real)(-r) * (Real)0.86602540378443864676;
-  auto wk = [&](const C* u, int x) {
-    C w;
-    if (x == 0) {
-      w = __ldg(u);
-      w.y = 0;
-      return w;
-    }
-    C p = __ldg(u + x), q = __ldg(u + (M - x));
-    q.y = -q.y;
-    if (r == 0) return cadd(p, q);
-    w = cadd(p, cmul(q, z3));
-    const C t = rt.at(x);
-    return r > 0 ? cmul(w, t) : cmulc(w, t);
-  };
+  const HermTerms ht(ri - 1);
   conv1_residue<M, E, TN>(
       i, A, rt,
       [&](int x, int) {
-        if (!act) {
-          C z;
-          z.x = 0;
-          z.y = 0;
-          return z;
-        }
-        const C wf = wk(f, x), wg = wk(g, x);
-        C v;   // w^f + i w^g
-        v.x = wf.x - wg.y;
-        v.y = wf.y + wg.x;
+        C v = ht.packed<M>(f, g, x, rt);
+        if (!act) v.x = v.y = 0;
         return v;
       },
       [&](int x, int, C v) {
         if (!act) return;
-        if (r != 0) {
-          const C t = rt.at(x);
-          v = r > 0 ? cmulc(v, t) : cmul(v, t);
-        }
-        v = cscale(v, sc);
-        if (ri == 0) hp[x] = v;
-        else if (ri == 1) hp[x] = cadd(hp[x], v);
-        else h[x] = cadd(hp[x], v);
+        v = cscale(ht.out(v, x, rt), sc);
+        // residue 0 writes the partial sum, 1 adds to it, 2 completes it in h
+        C prev;
+        prev.x = prev.y = 0;
+        if (ri) prev = hp[x];
+        (ri == 2 ? h : hp)[x] = cadd(prev, v);
       },
       sync);
 }
@@ -267,48 +293,22 @@ __device__ __noinline__ void l1_pair_residue(const FxArgs* a, int ri, int first,
   C* A = sm + gi * GS;
   const Real sc = (Real)1 / (Real)(3 * M);
   const GroupSync<T> sync{1 + gi};
-  const int r = ri - 1;
-  C z3;
-  z3.x = (Real)-0.5;
-  z3.y = (Real)(-r) * (Real)0.86602540378443864676;
-  auto wk = [&](const C* u, int x) {
-    C v;
-    if (x == 0) {
-      v = __ldg(u);
-      v.y = 0;
-      return v;
-    }
-    C p = __ldg(u + x), q = __ldg(u + (M - x));
-    q.y = -q.y;
-    if (r == 0) return cadd(p, q);
-    v = cadd(p, cmul(q, z3));
-    const C t = rt.at(x);
-    return r > 0 ? cmul(v, t) : cmulc(v, t);
-  };
+  const HermTerms ht(ri - 1);
   conv_pair_residue<M, E, TN>(
       i, A, A + PL, rt,
       [&](int x, int arr, int) {
-        C v;
-        v.x = 0;
-        v.y = 0;
-        if (!act) return v;
-        if (arr == 0) return wk(w, x);
-        const C wf = wk(f, x), wg = wk(g, x);
-        v.x = wf.x - wg.y;   // w^f + i w^g
-        v.y = wf.y + wg.x;
+        C v = arr == 0 ? ht.single<M>(w, x, rt) : ht.packed<M>(f, g, x, rt);
+        if (!act) v.x = v.y = 0;
         return v;
       },
       [&](int x, int, C v, int o) {
         if (!act) return;
-        if (r != 0) {
-          const C t = rt.at(x);
-          v = r > 0 ? cmulc(v, t) : cmul(v, t);
-        }
-        v = cscale(v, sc);
+        v = cscale(ht.out(v, x, rt), sc);
         C* p = o ? p1 : p0;
-        if (ri == 0) p[x] = v;
-        else if (ri == 1) p[x] = cadd(p[x], v);
-        else (o ? h1 : h0)[x] = cadd(p[x], v);
+        C prev;
+        prev.x = prev.y = 0;
+        if (ri) prev = p[x];
+        (ri == 2 ? (o ? h1 : h0) : p)[x] = cadd(prev, v);
       },
       sync);
 }
