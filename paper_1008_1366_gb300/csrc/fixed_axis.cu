@@ -56,14 +56,10 @@ __device__ __forceinline__ bool on_selfconj(const AxisArgs& a, int64_t i, int64_
   return false;
 }
 
-// element j of column i of the stored axis, projected onto (or, dbl,
-// doubled into) the Hermitian-symmetric subspace on the self-conjugate set
-__device__ __forceinline__ C load_sym(const AxisArgs& a, const C* in, int64_t o, int nin, int j, int64_t i,
-                                      bool dbl) {
-  const C v = in[(o * nin + j) * a.inner + i];
-  int64_t mi;
-  if (!on_selfconj(a, i, &mi)) return v;
-  const C u = in[(o * nin + (nin - 1 - j)) * a.inner + mi];
+// element v of a column on the self-conjugate set, with u the element at
+// its mirror (row nin-1-j of the mirror column): projected onto (or, dbl,
+// doubled into) the Hermitian-symmetric subspace, (v + conj u) / 2
+__device__ __forceinline__ C sym_part(C v, C u, bool dbl) {
   C s;
   s.x = v.x + u.x;
   s.y = v.y - u.y;
@@ -110,11 +106,21 @@ __global__ void __launch_bounds__(kThreads) axis_bwd_kernel(const __grid_constan
   if constexpr (!CEN) {
     // the column is read once; residue 1 multiplies it by zeta_{2m}^k
     C raw[E];
+    const C* base = in + o * (int64_t)nin * a.inner;
 #pragma unroll
     for (int b = 0; b < K::NB; ++b)
 #pragma unroll
       for (int q = 0; q < K::R; ++q)
-        raw[b * K::R + q] = act ? load_sym(a, in, o, nin, pos<L, E, 0, false>(i, b, q), col, dbl) : zero;
+        raw[b * K::R + q] = act ? base[(int64_t)pos<L, E, 0, false>(i, b, q) * a.inner + col] : zero;
+    int64_t mi = 0;
+    if (act && on_selfconj(a, col, &mi)) {
+#pragma unroll
+      for (int b = 0; b < K::NB; ++b)
+#pragma unroll
+        for (int q = 0; q < K::R; ++q)
+          raw[b * K::R + q] = sym_part(raw[b * K::R + q],
+                                       base[(int64_t)(nin - 1 - pos<L, E, 0, false>(i, b, q)) * a.inner + mi], dbl);
+    }
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
       C v[E];
@@ -132,10 +138,21 @@ __global__ void __launch_bounds__(kThreads) axis_bwd_kernel(const __grid_constan
       __syncthreads();
     }
   } else {
-    // stage the 2m-1 stored rows of the tile once (coalesced rows of W)
-    for (int e = threadIdx.x; e < nin * W; e += kThreads) {
-      const int j = e / W, cc = e - j * W;
-      stg[e] = i0 + cc < a.inner ? load_sym(a, in, o, nin, j, i0 + cc, dbl) : zero;
+    // stage the 2m-1 stored rows of the tile once (coalesced rows of W).  A
+    // thread keeps its column c for every row it stages, so the test for
+    // the self-conjugate set is made once, and the loads of its rows are
+    // independent of one another.
+    {
+      static_assert(kThreads % W == 0, "a thread keeps its column while staging");
+      int64_t mi = 0;
+      const bool sym = act && on_selfconj(a, col, &mi);
+      const C* base = in + o * (int64_t)nin * a.inner;
+#pragma unroll 8
+      for (int j = i; j < nin; j += kThreads / W) {
+        C v = act ? base[(int64_t)j * a.inner + col] : zero;
+        if (sym) v = sym_part(v, base[(int64_t)(nin - 1 - j) * a.inner + mi], dbl);
+        stg[j * W + c] = v;
+      }
     }
     __syncthreads();
 #pragma unroll 1
@@ -249,17 +266,13 @@ __global__ void __launch_bounds__(kThreads) axis_fwd_kernel(const __grid_constan
       });
       __syncthreads();
     }
-    // one scaled write of the tile (coalesced rows of W)
-    C* out = (C*)a.fout[z] + o * (int64_t)nout * a.inner;
-    for (int e = threadIdx.x; e < nout * W; e += kThreads) {
-      const int j = e / W, cc = e - j * W;
-      const int64_t cl = i0 + cc;
-      if (cl < a.inner) {
-        Real s = scale;
-        int64_t mm;
-        if (((a.halve_mask >> z) & 1) && on_selfconj(a, cl, &mm)) s *= (Real)0.5;
-        out[(int64_t)j * a.inner + cl] = cscale(H[e], s);
-      }
+    // one scaled write of the tile (coalesced rows of W); a thread keeps its
+    // column, whose scale sc was set above
+    static_assert(kThreads % W == 0, "a thread keeps its column while writing");
+    C* out = (C*)a.fout[z] + o * (int64_t)nout * a.inner + col;
+    if (act) {
+#pragma unroll 8
+      for (int j = i; j < nout; j += kThreads / W) out[(int64_t)j * a.inner] = cscale(H[j * W + c], sc);
     }
   }
 }
