@@ -240,15 +240,19 @@ __device__ __noinline__ void l1_residue(const FxArgs* a, int first, int count, C
 template <int M>
 __device__ __noinline__ void l1_herm_residue(const FxArgs* a, int ri, int first, int count, C* sm, Roots<C> rt) {
   using S = Shape<M>;
-  constexpr int E = S::E, T = S::T, GS = group_stride(M, T), TN = 3 * M;
+  constexpr int E = S::E, T = S::T, PL = padded(M), GS = group_stride(M, T), TN = 3 * M;
   const int gi = threadIdx.x / T, i = threadIdx.x % T;
   const bool act = gi < count;
   const int64_t off = act ? a->off[a->order[first + gi]] : 0;
   const C* f = (const C*)a->f + off;
   const C* g = (const C*)a->g + off;
   C* h = (C*)a->h + off;
-  C* hp = a->in_place ? (C*)a->tmp + (act ? a->l1tmp[a->order[first + gi]] : 0) : h;
   C* A = sm + gi * GS;
+  // The transform uses the group's first array only; the second holds the
+  // sum over the residues.  Output k of a thread sits at the same position
+  // in every residue, so the sum needs no barrier, and h is written once,
+  // at the last residue (after every read of f and g, so h may be f or g).
+  const Contig acc{A + PL};
   const Real sc = (Real)1 / (Real)(3 * M);
   const GroupSync<T> sync{1 + gi};
   const HermTerms ht(ri - 1);
@@ -260,13 +264,13 @@ __device__ __noinline__ void l1_herm_residue(const FxArgs* a, int ri, int first,
         return v;
       },
       [&](int x, int, C v) {
-        if (!act) return;
         v = cscale(ht.out(v, x, rt), sc);
-        // residue 0 writes the partial sum, 1 adds to it, 2 completes it in h
         C prev;
         prev.x = prev.y = 0;
-        if (ri) prev = hp[x];
-        (ri == 2 ? h : hp)[x] = cadd(prev, v);
+        if (ri) prev = acc[x];
+        v = cadd(prev, v);
+        if (ri < 2) acc[x] = v;
+        else if (act) h[x] = v;
       },
       sync);
 }
