@@ -506,10 +506,11 @@ __device__ __forceinline__ void conv1_residue(int i, C* Ap, const Roots<C>& rt, 
 // one residue of the rows of a centered Hermitian gradient (two Hermitian
 // convolutions sharing W, Sec. 2.3 applied to the adjoint): array A takes
 // W's packed input (its transform is real; the real part is kept), array B
-// w^f + i w^g.  The real products u^W u^g (output 0) and u^W u^f (output 1)
-// take one forward transform each; the second waits in B at the positions
-// where it was formed.  ld(x, arr, e) gives input arr at natural index x;
-// st(x, e, v, o) takes output o.
+// w^f + i w^g.  The real products a = u^W u^g (output 0) and b = u^W u^f
+// (output 1) share one forward transform Y of a + i b; since both are
+// real, their transforms are (Y_k + conj Y_{L-k}) / 2 and
+// (Y_k - conj Y_{L-k}) / 2i, read back through A.  ld(x, arr, e) gives
+// input arr at natural index x; st(x, e, v, o) takes output o.
 // ---------------------------------------------------------------------------
 template <int L, int E, int TN, class Ld, class St, class Sy>
 __device__ __forceinline__ void conv_pair_residue(int i, C* Ap, C* Bp, const Roots<C>& rt, const Ld& ld,
@@ -544,34 +545,38 @@ __device__ __forceinline__ void conv_pair_residue(int i, C* Ap, C* Bp, const Roo
     for (int q = 0; q < KB::R; ++q) {
       const int x = pos<L, E, n - 1, false>(i, b, q), e = b * KB::R + q;
       const Real uw = A[x].x;
-      C p1;
-      p1.x = uw * v[e].x;
-      p1.y = 0;
-      B[x] = p1;
-      v[e].x = uw * v[e].y;
-      v[e].y = 0;
+      const Real uf = v[e].x;
+      v[e].x = uw * v[e].y;   // u^W u^g
+      v[e].y = uw * uf;       // u^W u^f
     }
+  dft<L, E, 0, true, TN>(v, i, rt);
+  sync();
+  scatter<L, E, 0, true>(v, i, A);
+  sync();
+  one_middle<L, E, TN, true, 1>(v, i, true, A, rt, sync);
+  gather<L, E, n - 1, true>(v, i, A);
+  dft<L, E, n - 1, true, TN>(v, i, rt);
   using KF = Stage<L, E, n - 1, true>;
-#pragma unroll 1
-  for (int o = 0; o < 2; ++o) {
-    if (o == 1) {
+  sync();
 #pragma unroll
-      for (int b = 0; b < KB::NB; ++b)
+  for (int b = 0; b < KF::NB; ++b)
 #pragma unroll
-        for (int q = 0; q < KB::R; ++q) v[b * KB::R + q] = B[pos<L, E, n - 1, false>(i, b, q)];
+    for (int q = 0; q < KF::R; ++q) A[pos<L, E, n - 1, true>(i, b, q)] = v[b * KF::R + q];
+  sync();
+#pragma unroll
+  for (int b = 0; b < KF::NB; ++b)
+#pragma unroll
+    for (int q = 0; q < KF::R; ++q) {
+      const int x = pos<L, E, n - 1, true>(i, b, q), e = b * KF::R + q;
+      const C y = v[e], ym = A[x ? L - x : 0];
+      C o0, o1;
+      o0.x = (Real)0.5 * (y.x + ym.x);
+      o0.y = (Real)0.5 * (y.y - ym.y);
+      o1.x = (Real)0.5 * (y.y + ym.y);
+      o1.y = (Real)0.5 * (ym.x - y.x);
+      st(x, e, o0, 0);
+      st(x, e, o1, 1);
     }
-    dft<L, E, 0, true, TN>(v, i, rt);
-    sync();
-    scatter<L, E, 0, true>(v, i, A);
-    sync();
-    one_middle<L, E, TN, true, 1>(v, i, true, A, rt, sync);
-    gather<L, E, n - 1, true>(v, i, A);
-    dft<L, E, n - 1, true, TN>(v, i, rt);
-#pragma unroll
-    for (int b = 0; b < KF::NB; ++b)
-#pragma unroll
-      for (int q = 0; q < KF::R; ++q) st(pos<L, E, n - 1, true>(i, b, q), b * KF::R + q, v[b * KF::R + q], o);
-  }
 }
 
 // ---------------------------------------------------------------------------
