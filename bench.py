@@ -481,7 +481,7 @@ def main():
     peak, peak_kind = measured_peak_hbm()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": committed_traffic(alg_bytes), "peak_source": peak_kind,
-            "kernel": "dc::fx::fx_kernel (persistent task queue)",
+            "kernel": "dc::fx::f32::fx_kernel<0> (complex kind, persistent task queue)",
             "alg_bytes_per_launch": alg_bytes}
     if rank == 0:
         line = {
