@@ -1,5 +1,5 @@
-// Fixed-shape engine: FP32 complex implicitly dealiased convolutions whose
-// sizes are known at compile time.
+// Fixed-shape engine: implicitly dealiased convolutions (FP32 and FP64
+// builds) whose sizes are known at compile time.
 //
 // Every size m of the set {2^a, 3*2^a, 5*2^a} in [64, 65536] gets its own
 // code: radices, threads per transform, tile shapes and every shared-memory

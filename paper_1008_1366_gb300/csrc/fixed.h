@@ -1,5 +1,5 @@
-// Host interface of the fixed-shape FP32 complex engine (fixed.cuh,
-// fixed_batched.cu): task records, kernel arguments, planning, launch.
+// Host interface of the fixed-shape engine (fixed.cuh, fixed_batched.cu;
+// FP32 and FP64 builds): task records, kernel arguments, planning, launch.
 #pragma once
 
 #include <cuda_runtime.h>

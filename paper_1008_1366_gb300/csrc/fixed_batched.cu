@@ -1,5 +1,7 @@
-// Persistent task-queue kernel of the fixed-shape FP32 complex engine and
-// its host-side planner.
+// Persistent task-queue kernel of the fixed-shape engine (compiled once per
+// precision; one instantiation per kind of convolution: binary complex,
+// centered Hermitian, ternary, Hermitian gradient rows) and its host-side
+// planner.
 //
 // The queue holds level-1 tasks (a group of same-size instances wholly in
 // shared memory) and the three pass tasks of every level-2 instance (column

@@ -31,7 +31,6 @@ bool fx_uniform_ok(int64_t m, int ds);
 bool fx_uniform_two_level(int64_t m);   // m runs as row/column passes spread over many blocks
 // mode: the fixed engine's kind of convolution (fx::MODE_*, 0 = binary complex)
 size_t fx_uniform_work(int64_t n, int64_t m, int ds, int mode = 0);
-// herm: centered Hermitian convolutions (level-1 sizes only)
 dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, struct dc_batched_plan** out, int mode = 0);
 // the rows of a centered Hermitian gradient on a MODE_PAIR plan:
 // df = conv(w, g), dg = conv(w, f); outputs may be inputs
