@@ -141,11 +141,17 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# the translation unit of fx_kernel: its source and every header it includes
+FX_KERNEL_SOURCES = ["paper_1008_1366_gb300/csrc/fixed_batched.cu", "paper_1008_1366_gb300/csrc/fixed.cuh",
+                     "paper_1008_1366_gb300/csrc/fixed.h", "paper_1008_1366_gb300/csrc/fft2.cuh",
+                     "paper_1008_1366_gb300/csrc/fft.cuh", "paper_1008_1366_gb300/csrc/common.cuh",
+                     "paper_1008_1366_gb300/csrc/launch.h", "include/dealias.h"]
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1008_1366_gb300", "csrc")
-    for n in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, n), "rb").read())
+    for n in FX_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, n), "rb").read())
     return h.hexdigest()[:16]
 
 
