@@ -9,6 +9,11 @@
 //            for k = -m+1..m-1.
 // A block of 256 threads owns one outer index and a tile of W consecutive
 // inner indices (columns); W = 256 E / m, T = m / E threads per column.
+// Complex axes take E = 16; centered axes, whose tiles also hold the 2m-1
+// staged input rows, take E = 8 up to m = 512 (half the columns, half the
+// shared memory, twice the resident blocks), where a tile row still fills
+// whole 32-byte sectors (W >= 4); at m = 1024 that halving cost more in
+// half-used sectors than it gained (2D 1024^2: 0.208 -> 0.228 ms).
 // Every stage is compile-time code on registers (no runtime plan), the
 // input columns are read once for all residues, and the forward direction
 // recombines the residues in shared memory before one scaled write.
@@ -25,9 +30,8 @@ namespace DC_FX_P {
 
 namespace {
 
-constexpr int kAxisE = 16;
-template <int L> struct AxisShape {
-  static constexpr int E = kAxisE;
+template <int L, bool CEN> struct AxisShape {
+  static constexpr int E = CEN && L <= 512 ? 8 : 16;
   static constexpr int T = L / E;
   static constexpr int W = kThreads * E / L;
   static_assert(L % E == 0 && W >= 1 && W * T == kThreads, "axis tile covers the block");
@@ -39,10 +43,11 @@ __host__ __device__ constexpr int axis_ceil_log2(int x) {
   return l;
 }
 
-// shared memory: roots, transform buffer (W L), staged input or
-// recombination buffer ((2m-1) W)
-template <int L> constexpr int axis_smem_bytes() {
-  return (kRootsMax + AxisShape<L>::W * L + (2 * L - 1) * AxisShape<L>::W) * (int)sizeof(C);
+// shared memory: roots, transform buffer (W L), and for centered axes the
+// staged input or recombination buffer ((2m-1) W)
+template <int L, bool CEN> constexpr int axis_smem_bytes() {
+  using S = AxisShape<L, CEN>;
+  return (kRootsMax + S::W * L + (CEN ? (2 * L - 1) * S::W : 0)) * (int)sizeof(C);
 }
 
 __device__ __forceinline__ bool on_selfconj(const AxisArgs& a, int64_t i, int64_t* mirror) {
@@ -83,7 +88,7 @@ __device__ __forceinline__ Roots<C> fill_roots(const AxisArgs& a, C* rts) {
 
 template <int L, bool CEN>
 __global__ void __launch_bounds__(kThreads) axis_bwd_kernel(const __grid_constant__ AxisArgs a) {
-  using S = AxisShape<L>;
+  using S = AxisShape<L, CEN>;
   constexpr int E = S::E, W = S::W, TN = (CEN ? 3 : 2) * L, nin = CEN ? 2 * L - 1 : L;
   using K = Stage<L, E, 0, false>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) axis_bwd_kernel(const __grid_constan
 
 template <int L, bool CEN>
 __global__ void __launch_bounds__(kThreads) axis_fwd_kernel(const __grid_constant__ AxisArgs a) {
-  using S = AxisShape<L>;
+  using S = AxisShape<L, CEN>;
   constexpr int E = S::E, W = S::W, q = CEN ? 3 : 2, TN = q * L, nout = CEN ? 2 * L - 1 : L;
   using K = Stage<L, E, 0, true>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -277,25 +282,24 @@ __global__ void __launch_bounds__(kThreads) axis_fwd_kernel(const __grid_constan
   }
 }
 
-template <int L>
-dc_status launch_L(bool forward, const AxisArgs& a, int narrays, cudaStream_t s) {
-  using S = AxisShape<L>;
+template <int L, bool CEN>
+dc_status launch_LC(bool forward, const AxisArgs& a, int narrays, cudaStream_t s) {
+  using S = AxisShape<L, CEN>;
   const int64_t tiles = a.outer * ((a.inner + S::W - 1) / S::W);
   if (tiles < 1 || narrays < 1) return DC_OK;
   if (tiles > 0x7fffffff) return DC_ERR_SIZE;
-  constexpr int smem = axis_smem_bytes<L>();
+  constexpr int smem = axis_smem_bytes<L, CEN>();
   dim3 grid((unsigned)tiles, (unsigned)narrays);
-  if (a.centered) {
-    auto k = forward ? axis_fwd_kernel<L, true> : axis_bwd_kernel<L, true>;
-    DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k<<<grid, kThreads, smem, s>>>(a);
-  } else {
-    auto k = forward ? axis_fwd_kernel<L, false> : axis_bwd_kernel<L, false>;
-    DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k<<<grid, kThreads, smem, s>>>(a);
-  }
+  auto k = forward ? axis_fwd_kernel<L, CEN> : axis_bwd_kernel<L, CEN>;
+  DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  k<<<grid, kThreads, smem, s>>>(a);
   DC_CUDA_TRY(cudaGetLastError());
   return DC_OK;
+}
+
+template <int L>
+dc_status launch_L(bool forward, const AxisArgs& a, int narrays, cudaStream_t s) {
+  return a.centered ? launch_LC<L, true>(forward, a, narrays, s) : launch_LC<L, false>(forward, a, narrays, s);
 }
 
 }  // namespace

@@ -57,6 +57,31 @@ def test_hermitian_nd(dc, ms, dtype):
     assert rel_l2(h, oracle.conv_hermitian(f, g)) <= tol(dtype, np.prod([3 * m for m in ms]))
 
 
+# outer axes of every length the compile-time outer-axis kernels cover
+# (2^a, 64..4096; centered axes take 8 elements per thread up to 512)
+OUTER_H = [(128, 4), (256, 3), (512, 2), (2048, 2), (4096, 2), (128, 3, 4), (3, 128, 4), (64, 64, 2)]
+OUTER_C = [(128, 3), (256, 5), (512, 2), (1024, 2), (4096, 2), (128, 64, 2)]
+
+
+@pytest.mark.parametrize("ms", OUTER_H)
+@pytest.mark.parametrize("dtype", DT)
+def test_hermitian_nd_outer_lengths(dc, ms, dtype):
+    shape = synthetic.hermitian_shape(ms)
+    f = synthetic.hermitian_spectrum(shape, 1.5, 15)
+    g = synthetic.hermitian_spectrum(shape, 1.5, 16)
+    h = dc.conv_hermitian_nd(dev(f, dtype), dev(g, dtype)).cpu().numpy()
+    assert rel_l2(h, oracle.padded_hermitian(f, g)) <= tol(dtype, np.prod([3 * m for m in ms]))
+
+
+@pytest.mark.parametrize("shape", OUTER_C)
+@pytest.mark.parametrize("dtype", DT)
+def test_complex_nd_outer_lengths(dc, shape, dtype):
+    f = synthetic.uniform_complex(shape, 17)
+    g = synthetic.uniform_complex(shape, 18)
+    h = dc.conv_complex_nd(dev(f, dtype), dev(g, dtype)).cpu().numpy()
+    assert rel_l2(h, oracle.padded_complex(f, g)) <= tol(dtype, np.prod([2 * m for m in shape]))
+
+
 # wide rows: the row convolutions run on the fixed-shape engine (every
 # size family, both precisions)
 HW = [(2, 64), (2, 80), (3, 96), (2, 640), (2, 1536), (2, 4096), (2, 6144), (4, 5120), (2, 3, 256), (2, 8192),
