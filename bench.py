@@ -165,6 +165,8 @@ def committed_traffic(total_bytes_alg):
         return None
     if rec.get("source_hash") != kernel_source_hash():
         return None
+    if rec.get("alg_bytes_per_launch") != total_bytes_alg:   # another workload
+        return None
     return rec.get("traffic_bytes_per_launch")
 
 
