@@ -76,6 +76,25 @@ def brute_hermitian_nd(f, g):
     return out
 
 
+def brute_ternary_nd(f, g, e):
+    """h_k = sum_{p+q+r=k} f_p g_q e_r over the box |p_d|, |q_d|, |r_d| <= m_d-1,
+    at the stored wave vectors k, written out from the problem statement."""
+    ms = [(n + 1) // 2 for n in f.shape[:-1]] + [f.shape[-1]]
+    box = list(itertools.product(*[range(-m + 1, m) for m in ms]))
+    out = np.zeros(f.shape, dtype=np.complex128)
+    for idx in np.ndindex(*f.shape):
+        k = [idx[a] - (ms[a] - 1) for a in range(len(ms) - 1)] + [idx[-1]]
+        s = 0
+        for p in box:
+            fp = value_nd(f, p)
+            for q in box:
+                r = [k[a] - p[a] - q[a] for a in range(len(ms))]
+                if all(abs(r[a]) <= ms[a] - 1 for a in range(len(ms))):
+                    s += fp * value_nd(g, q) * value_nd(e, r)
+        out[idx] = s
+    return out
+
+
 # --- 1D ----------------------------------------------------------------------
 
 @pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6, 8, 12, 16, 20, 32, 64])
@@ -240,6 +259,17 @@ def test_ternary_brute_force_exact(m):
     exact = brute_ternary_1d(f, g, e)
     assert np.max(np.abs(oracle.direct_ternary_hermitian(f, g, e) - exact)) < 1e-11
     assert np.max(np.abs(oracle.padded_ternary_hermitian(f, g, e) - exact)) < 1e-10
+
+
+@pytest.mark.parametrize("ms", [(2, 2), (2, 3), (3, 2), (3, 3), (2, 2, 2)])
+def test_ternary_nd_brute_force_exact(ms):
+    # the multi-D ternary case (the outer axes centered, the last one the
+    # Hermitian half axis), on Gaussian integers so that the sums are exact
+    shape = synthetic.hermitian_shape(ms)
+    f, g, e = (gaussian_ints(shape, s) for s in (4, 5, 6))
+    exact = brute_ternary_nd(f, g, e)
+    assert np.max(np.abs(oracle.direct_ternary_hermitian(f, g, e) - exact)) < 1e-10
+    assert np.max(np.abs(oracle.padded_ternary_hermitian(f, g, e) - exact)) < 1e-9
 
 
 @pytest.mark.parametrize("m", [16, 256, 2 ** 14])
