@@ -38,6 +38,8 @@ from .conv import (  # noqa: F401
     conv_complex,
     conv_hermitian,
     conv_ternary_hermitian,
+    dot_complex,
+    dot_hermitian,
 )
 from .adjoint import (  # noqa: F401
     loss,

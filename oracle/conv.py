@@ -269,3 +269,23 @@ def conv_ternary_hermitian(f, g, e):
     if n * n <= _DIRECT_LIMIT // 4:
         return direct_ternary_hermitian(f, g, e)
     return padded_ternary_hermitian(f, g, e)
+
+
+# ---------------------------------------------------------------------------
+# inputs as arrays of vectors (Sec. 3, 2D pseudospectral application): the
+# product f * g read as the dot product sum_i f_i * g_i of M pairs
+# ---------------------------------------------------------------------------
+
+def dot_complex(fs, gs):
+    """sum_i conv_complex(f_i, g_i) over the M pairs (f_i, g_i)."""
+    if len(fs) != len(gs) or not fs:
+        raise ValueError("need M >= 1 pairs")
+    return sum(conv_complex(f, g) for f, g in zip(fs, gs))
+
+
+def dot_hermitian(fs, gs):
+    """sum_i conv_hermitian(f_i, g_i) over the M pairs (f_i, g_i)."""
+    if len(fs) != len(gs) or not fs:
+        raise ValueError("need M >= 1 pairs")
+    return sum(conv_hermitian(f, g) for f, g in zip(fs, gs))
+
