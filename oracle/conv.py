@@ -30,7 +30,25 @@ by the orthogonal projection ``project_hermitian`` onto the symmetric subspace
 last-axis-zero row/plane in 2D/3D).
 """
 
+import os
+
 import numpy as np
+
+try:   # a threaded library FFT where scipy is present; numpy's otherwise
+    import scipy.fft as _sfft
+    FFT_LIBRARY = "scipy.fft"
+except ImportError:   # pragma: no cover
+    _sfft = None
+    FFT_LIBRARY = "numpy.fft"
+
+
+def _fftn(a, inverse=False):
+    """Library n-dimensional DFT (a step of the padded convolution): numpy's
+    sign and scaling conventions (forward e^{-2 pi i jk/N}, inverse with 1/N)."""
+    if _sfft is not None:
+        fn = _sfft.ifftn if inverse else _sfft.fftn
+        return fn(a, workers=os.cpu_count() or 1, overwrite_x=True)
+    return np.fft.ifftn(a) if inverse else np.fft.fftn(a)
 
 
 def _c(a):
@@ -139,9 +157,14 @@ def _padded_box(arrays, los, N, out_lo, out_shape):
         P = np.zeros(N, dtype=np.complex128)
         idx = tuple((np.arange(A.shape[a]) + lo[a]) % N[a] for a in range(d))
         P[np.ix_(*idx)] = A
-        T = np.fft.fftn(P)
-        prod = T if prod is None else prod * T
-    H = np.fft.ifftn(prod)
+        T = _fftn(P)
+        del P
+        if prod is None:
+            prod = T
+        else:
+            prod *= T
+        del T
+    H = _fftn(prod, inverse=True)
     oidx = tuple((np.arange(out_shape[a]) + out_lo[a]) % N[a] for a in range(d))
     return H[np.ix_(*oidx)]
 

@@ -144,6 +144,25 @@ def test_numpy_fft_parseval():
     assert np.max(abs(np.fft.ifft(X) - x)) < 1e-12
 
 
+def test_oracle_fft_step_is_the_dft():
+    # the padded oracle's library FFT step (scipy's threaded FFT where present):
+    # the DFT by its definition on a small 3D grid (both signs, inverse scaled
+    # by 1/N), then Parseval and the round trip at a size with factors 2, 3
+    from oracle.conv import _fftn
+    x = gaussian_ints((4, 6, 3), 8)
+    n = x.shape
+    ks = [np.arange(v) for v in n]
+    W = [np.exp(-2j * np.pi * np.outer(k, k) / len(k)) for k in ks]
+    X = np.einsum("ai,bj,ck,ijk->abc", W[0], W[1], W[2], x)
+    assert np.max(abs(_fftn(x.copy()) - X)) < 1e-11
+    Xi = np.einsum("ai,bj,ck,ijk->abc", W[0].conj(), W[1].conj(), W[2].conj(), x) / x.size
+    assert np.max(abs(_fftn(x.copy(), inverse=True) - Xi)) < 1e-12
+    y = gaussian_ints((48, 36), 9)
+    Y = _fftn(y.copy())
+    assert abs(y.size * np.sum(abs(y) ** 2) - np.sum(abs(Y) ** 2)) < 1e-9 * np.sum(abs(Y) ** 2)
+    assert np.max(abs(_fftn(Y, inverse=True) - y)) < 1e-11
+
+
 def test_golden_paper_closed_forms():
     # tests/golden/paper_closed_forms.txt: the exact solutions of the paper's
     # accuracy tests (Sec. 2.1 and Sec. 2.3) at m = 8
