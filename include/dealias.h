@@ -74,6 +74,26 @@ int32_t dc_last_cuda_error(void);
 dc_status dc_workspace_size(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype,
                             size_t* bytes);
 
+/* 3D calls (Sec. 3.4) run the x-level residue slabs through their (y, z) work
+ * arrays a chunk of slabs at a time, reusing the work arrays chunk after
+ * chunk (the decoupled work arrays of Sec. 1 and Sec. 3.1).  The chunk size
+ * follows the workspace the caller passes: the size dc_workspace_size reports
+ * holds the default chunk (about 512 MB of work arrays); a smaller workspace
+ * gives smaller chunks, down to one slab (3 m_x slabs for Hermitian kinds,
+ * 2 m_x for complex ones), with the same result.
+ * dc_workspace_size_slabs: workspace bytes of a 3D call of `kind` on dims
+ * (ndim must be 3) whose chunks hold at most slabs_per_chunk (>= 1) slabs;
+ * slabs_per_chunk = 1 gives the smallest workspace a 3D call accepts.
+ * dc_chunking: the chunking a call of `kind` on dims makes with work_bytes of
+ * workspace: *slabs_per_chunk and *chunks (the last chunk holds the rest);
+ * *chunks = 0 when the workspace is too small for any call (which then
+ * returns DC_ERR_NOMEM).  2D calls have one pass: *slabs_per_chunk = 0 and
+ * *chunks = 1 when work_bytes suffices.  DC_ERR_ARG / DC_ERR_SIZE as above. */
+dc_status dc_workspace_size_slabs(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype,
+                                  int64_t slabs_per_chunk, size_t* bytes);
+dc_status dc_chunking(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype, size_t work_bytes,
+                      int64_t* slabs_per_chunk, int64_t* chunks);
+
 /* Builds the root tables for a call of `kind` on dims (allocates device
  * memory once per size and device).  Optional; the first call does it too. */
 dc_status dc_prepare(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype);
@@ -263,6 +283,18 @@ dc_status dc_conv_complex_1d_batched_host(dc_batched_plan* plan, const void* hf,
                                           void* df, void* dg, void* dh, void* work, size_t work_bytes,
                                           int32_t nchunks, void* stream);
 dc_status dc_batched_plan_destroy(dc_batched_plan* plan);
+
+/* Partition of a batch of independent 1D convolutions across nranks
+ * processes (one per GPU) by the longest-processing-time rule: instances
+ * in order of decreasing cost m log2 m (the sub-transforms' operation count,
+ * Sec. 2.1), equal costs in instance order, each to the rank with the least
+ * load so far (ties: the lowest rank).  No counterpart in the paper (a
+ * scheduling choice for running one batch on several GPUs, each rank then
+ * planning and convolving its own instances with no exchange of data).
+ * m: n sizes (host, >= 1).  owner: n ranks written (host).  load: nranks
+ * summed costs written (host), or NULL.  Host code only: needs no GPU.
+ * DC_ERR_ARG for n < 0, nranks < 1, a size < 1 or a NULL array with n > 0. */
+dc_status dc_partition_lpt(const int64_t* m, int32_t n, int32_t nranks, int32_t* owner, double* load);
 
 #ifdef __cplusplus
 }

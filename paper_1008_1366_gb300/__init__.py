@@ -6,6 +6,7 @@ include/dealias.h); this package is its thin PyTorch binding.
 
 from .api import (  # noqa: F401
     BatchedPlan,
+    chunking,
     DealiasError,
     conv_complex_1d,
     conv_complex_1d_adjoint,
@@ -16,8 +17,11 @@ from .api import (  # noqa: F401
     conv_hermitian_1d,
     conv_hermitian_1d_adjoint,
     conv_ternary_hermitian_1d,
+    partition_lpt,
     prepare,
     read_status,
     read_trace,
+    shard,
     workspace_size,
+    workspace_size_slabs,
 )

@@ -21,6 +21,8 @@ SIGNATURES = {
     "dc_last_cuda_error": [],
     "dc_workspace_size": [_i32, _i32, ctypes.POINTER(_i64), _i32, ctypes.POINTER(_sz)],
     "dc_prepare": [_i32, _i32, ctypes.POINTER(_i64), _i32],
+    "dc_workspace_size_slabs": [_i32, _i32, ctypes.POINTER(_i64), _i32, _i64, ctypes.POINTER(_sz)],
+    "dc_chunking": [_i32, _i32, ctypes.POINTER(_i64), _i32, _sz, ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "dc_read_status": [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "dc_conv_complex_1d": [_vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_hermitian_1d": [_vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
@@ -48,6 +50,7 @@ SIGNATURES = {
     "dc_conv_complex_1d_batched_host": [_vp] + [_vp] * 7 + [_sz, _i32, _vp],
     "dc_conv_complex_1d_batched": [_vp, _vp, _vp, _vp, _vp, _sz, _vp],
     "dc_batched_plan_destroy": [_vp],
+    "dc_partition_lpt": [ctypes.POINTER(_i64), _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)],
 }
 _RET = {"dc_status_string": ctypes.c_char_p}
 

@@ -69,6 +69,25 @@ def workspace_size(kind, dims, dtype):
     return int(out.value)
 
 
+def workspace_size_slabs(kind, dims, dtype, slabs_per_chunk):
+    """Workspace of a 3D call whose chunks hold at most this many x-slabs
+    (dc_workspace_size_slabs)."""
+    d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    out = ctypes.c_size_t(0)
+    check(_native.lib().dc_workspace_size_slabs(kind, len(dims), d, dtype, int(slabs_per_chunk),
+                                                ctypes.byref(out)), "dc_workspace_size_slabs")
+    return int(out.value)
+
+
+def chunking(kind, dims, dtype, work_bytes):
+    """(slabs per chunk, chunks) of a multi-D call with this workspace (dc_chunking)."""
+    d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    s, c = ctypes.c_int64(0), ctypes.c_int64(0)
+    check(_native.lib().dc_chunking(kind, len(dims), d, dtype, int(work_bytes), ctypes.byref(s), ctypes.byref(c)),
+          "dc_chunking")
+    return int(s.value), int(c.value)
+
+
 def prepare(kind, dims, dtype):
     d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
     check(_native.lib().dc_prepare(kind, len(dims), d, dtype), "dc_prepare")
@@ -146,13 +165,16 @@ def _dims(t, hermitian):
     return [(n + 1) // 2 for n in shape[:-1]] + [shape[-1]]
 
 
-def _run_md(name, kind, ins, nout, hermitian):
+def _run_md(name, kind, ins, nout, hermitian, slabs_per_chunk=None):
     dt = _inputs(*ins)
     if ins[0].dim() not in (2, 3):
         raise ValueError(f"{name}: expected 2D or 3D tensors")
     dims = _dims(ins[0], hermitian)
     outs = [torch.empty_like(ins[0]) for _ in range(nout)]
-    ws = workspace_size(kind, dims, dt)
+    if slabs_per_chunk is not None and len(dims) == 3:
+        ws = workspace_size_slabs(kind, dims, dt, slabs_per_chunk)
+    else:
+        ws = workspace_size(kind, dims, dt)
     work = _work(ws, ins[0].device)
     fn = getattr(_native.lib(), name)
     args = [_vp(t) for t in ins] + [_vp(t) for t in outs] + list(dims)
@@ -160,24 +182,47 @@ def _run_md(name, kind, ins, nout, hermitian):
     return outs[0] if nout == 1 else tuple(outs)
 
 
-def conv_complex_nd(f, g):
+# slabs_per_chunk (3D only): a workspace sized for chunks of at most that
+# many x-slabs (dc_workspace_size_slabs) instead of the default.
+
+def conv_complex_nd(f, g, slabs_per_chunk=None):
     """2D/3D complex convolution (dc_conv_complex_2d / _3d)."""
-    return _run_md(f"dc_conv_complex_{f.dim()}d", KIND_COMPLEX, [f, g], 1, False)
+    return _run_md(f"dc_conv_complex_{f.dim()}d", KIND_COMPLEX, [f, g], 1, False, slabs_per_chunk)
 
 
-def conv_hermitian_nd(f, g):
+def conv_hermitian_nd(f, g, slabs_per_chunk=None):
     """2D/3D centered Hermitian convolution (dc_conv_hermitian_2d / _3d)."""
-    return _run_md(f"dc_conv_hermitian_{f.dim()}d", KIND_HERMITIAN, [f, g], 1, True)
+    return _run_md(f"dc_conv_hermitian_{f.dim()}d", KIND_HERMITIAN, [f, g], 1, True, slabs_per_chunk)
 
 
-def conv_complex_nd_adjoint(w, f, g):
+def conv_complex_nd_adjoint(w, f, g, slabs_per_chunk=None):
     """(df, dg) for the 2D/3D complex convolution."""
-    return _run_md(f"dc_conv_complex_{f.dim()}d_adjoint", KIND_COMPLEX_ADJOINT, [w, f, g], 2, False)
+    return _run_md(f"dc_conv_complex_{f.dim()}d_adjoint", KIND_COMPLEX_ADJOINT, [w, f, g], 2, False,
+                   slabs_per_chunk)
 
 
-def conv_hermitian_nd_adjoint(w, f, g):
+def conv_hermitian_nd_adjoint(w, f, g, slabs_per_chunk=None):
     """(df, dg) for the 2D/3D centered Hermitian convolution."""
-    return _run_md(f"dc_conv_hermitian_{f.dim()}d_adjoint", KIND_HERMITIAN_ADJOINT, [w, f, g], 2, True)
+    return _run_md(f"dc_conv_hermitian_{f.dim()}d_adjoint", KIND_HERMITIAN_ADJOINT, [w, f, g], 2, True,
+                   slabs_per_chunk)
+
+
+def partition_lpt(sizes, nranks):
+    """Owner rank of every instance and the per-rank summed costs
+    (dc_partition_lpt: longest processing time first, cost m log2 m)."""
+    n = len(sizes)
+    m = (ctypes.c_int64 * max(n, 1))(*[int(x) for x in sizes])
+    owner = (ctypes.c_int32 * max(n, 1))()
+    load = (ctypes.c_double * int(nranks))()
+    check(_native.lib().dc_partition_lpt(m, n, int(nranks), owner, load), "dc_partition_lpt")
+    return [int(owner[i]) for i in range(n)], [float(load[r]) for r in range(int(nranks))]
+
+
+def shard(sizes, rank, world):
+    """Instance ids (in instance order) that rank `rank` of `world` convolves
+    when one batch is split across processes by partition_lpt."""
+    owner, _ = partition_lpt(sizes, world)
+    return [i for i, o in enumerate(owner) if o == rank]
 
 
 class BatchedPlan:

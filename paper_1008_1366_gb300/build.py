@@ -16,7 +16,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdealias.so")
 
-SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu",
+           "partition.cu"]
 # the fixed-shape engine, one translation unit per precision
 FIXED = [(src, src.replace(".cu", f"_{tag}.o"), [f"-DDC_FX_P={ns}", f"-DDC_FX_C={c}"])
          for src in ("fixed_batched.cu", "fixed_axis.cu")

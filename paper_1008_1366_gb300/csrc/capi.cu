@@ -221,6 +221,22 @@ dc_status dc_workspace_size(int32_t kind, int32_t ndim, const int64_t* dims, int
   return plan_1d(k, dims[0], ds, false, &cfg, bytes);
 }
 
+dc_status dc_workspace_size_slabs(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype,
+                                  int64_t slabs_per_chunk, size_t* bytes) {
+  const int ds = dsize_of(dtype);
+  const int k = kind_of_public(kind);
+  if (!ds || k < 0 || !dims || !bytes || ndim != 3 || slabs_per_chunk < 1) return DC_ERR_ARG;
+  return md_workspace_slabs(kind, ndim, dims, ds, slabs_per_chunk, bytes);
+}
+
+dc_status dc_chunking(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype, size_t work_bytes,
+                      int64_t* slabs_per_chunk, int64_t* chunks) {
+  const int ds = dsize_of(dtype);
+  const int k = kind_of_public(kind);
+  if (!ds || k < 0 || !dims || !slabs_per_chunk || !chunks || ndim < 2 || ndim > 3) return DC_ERR_ARG;
+  return md_chunking(kind, ndim, dims, ds, work_bytes, slabs_per_chunk, chunks);
+}
+
 dc_status dc_prepare(int32_t kind, int32_t ndim, const int64_t* dims, int32_t dtype) {
   const int ds = dsize_of(dtype);
   const int k = kind_of_public(kind);

@@ -89,7 +89,10 @@ bool axis_cfg(bool centered, int64_t m, int ds, bool with_table, AxisArgs* a) {
   return true;
 }
 
-dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_tables, Md* md) {
+// slabs_req > 0 (3D only): run the (y, z) work arrays for at most that many
+// x-slabs per chunk instead of the default budget's count.
+dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_tables, Md* md,
+                  int64_t slabs_req = 0) {
   if (ndim < 2 || ndim > 3) return DC_ERR_ARG;
   for (int d = 0; d < ndim; ++d) {
     if (dims[d] < 1) return DC_ERR_ARG;
@@ -118,6 +121,7 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
     md->sx = md->ny_in * mlast;
     const size_t per_slab = (size_t)md->narr * md->qa * my * mlast * ds;
     md->S = std::max<int64_t>(1, std::min<int64_t>(md->slabs, kChunkBudget / per_slab));
+    if (slabs_req > 0) md->S = std::min<int64_t>(slabs_req, md->slabs);
     nrows = md->qa * md->S * my;
   }
   if (!make_cfg(md->row_kind, mlast, ds, kThreads, smem_cap(), 0, &md->rows)) return DC_ERR_SIZE;
@@ -205,6 +209,50 @@ dc_status md_workspace(int pk, int ndim, const int64_t* dims, int ds, size_t* by
   return st;
 }
 
+dc_status md_workspace_slabs(int pk, int ndim, const int64_t* dims, int ds, int64_t slabs, size_t* bytes) {
+  if (slabs < 1) return DC_ERR_ARG;
+  Md md;
+  dc_status st = plan_md(pk, ndim, dims, ds, false, &md, ndim == 3 ? slabs : 0);
+  if (st == DC_OK) *bytes = md.total;
+  return st;
+}
+
+// Slabs per chunk of a call given work_bytes of workspace: the default
+// count when the workspace holds it, else the largest count whose
+// workspace fits (the workspace grows with the count), 0 when not even one
+// slab fits.
+dc_status md_chunking(int pk, int ndim, const int64_t* dims, int ds, size_t work_bytes, int64_t* slabs,
+                      int64_t* chunks) {
+  Md md;
+  dc_status st = plan_md(pk, ndim, dims, ds, false, &md);
+  if (st != DC_OK) return st;
+  if (ndim == 2) {
+    *slabs = 0;
+    *chunks = work_bytes >= md.total ? 1 : 0;
+    return DC_OK;
+  }
+  int64_t S = 0;
+  if (work_bytes >= md.total) {
+    S = md.S;
+  } else {
+    int64_t lo = 1, hi = md.S - 1;
+    while (lo <= hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      Md t;
+      if ((st = plan_md(pk, ndim, dims, ds, false, &t, mid)) != DC_OK) return st;
+      if (t.total <= work_bytes) {
+        S = mid;
+        lo = mid + 1;
+      } else {
+        hi = mid - 1;
+      }
+    }
+  }
+  *slabs = S;
+  *chunks = S ? (md.slabs + S - 1) / S : 0;
+  return DC_OK;
+}
+
 dc_status md_prepare(int pk, int ndim, const int64_t* dims, int ds) {
   Md md;
   return plan_md(pk, ndim, dims, ds, true, &md);
@@ -212,8 +260,13 @@ dc_status md_prepare(int pk, int ndim, const int64_t* dims, int ds) {
 
 dc_status md_run(int pk, int ndim, const int64_t* dims, int ds, const void* const* ins, int nin,
                  void* const* outs, int nout, void* work, size_t work_bytes, cudaStream_t s) {
+  // 3D: the chunk of x-slabs whose (y, z) work arrays the workspace holds
+  int64_t S = 0, nchunks = 0;
+  dc_status st = md_chunking(pk, ndim, dims, ds, work_bytes, &S, &nchunks);
+  if (st != DC_OK) return st;
+  if (nchunks == 0) return DC_ERR_NOMEM;
   Md md;
-  dc_status st = plan_md(pk, ndim, dims, ds, true, &md);
+  st = plan_md(pk, ndim, dims, ds, true, &md, S);
   if (st != DC_OK) return st;
   if (nin != md.narr || nout != md.nout) return DC_ERR_ARG;
   if (work_bytes < md.total) return DC_ERR_NOMEM;

@@ -44,6 +44,9 @@ namespace f64 { dc_status launch_axis_fixed(bool forward, const AxisArgs& a, int
 
 // public multi-D kinds handled by multid.cu
 dc_status md_workspace(int pkind, int ndim, const int64_t* dims, int ds, size_t* bytes);
+dc_status md_workspace_slabs(int pkind, int ndim, const int64_t* dims, int ds, int64_t slabs, size_t* bytes);
+dc_status md_chunking(int pkind, int ndim, const int64_t* dims, int ds, size_t work_bytes, int64_t* slabs,
+                      int64_t* chunks);
 dc_status md_prepare(int pkind, int ndim, const int64_t* dims, int ds);
 dc_status md_run(int pkind, int ndim, const int64_t* dims, int ds, const void* const* ins, int nin,
                  void* const* outs, int nout, void* work, size_t work_bytes, cudaStream_t s);

@@ -15,6 +15,8 @@ Recipes:
 * ``batched_sizes``: sizes drawn uniformly from the 31 members of
   {2^k, 3*2^k, 5*2^k} in [64, 65536] (a discrete log-uniform law, since the
   members are nearly evenly spaced in log m).
+* ``instance_inputs``: uniform[-1, 1] entries of chosen instances of a batch,
+  each instance from its own seeded stream (a rank's share alone).
 """
 
 import numpy as np
@@ -87,6 +89,26 @@ def batched_sizes(n, seed, sizes=None):
     sizes = SIZES_31 if sizes is None else sizes
     r = rng(seed)
     return np.asarray(sizes, dtype=np.int64)[r.integers(0, len(sizes), size=int(n))]
+
+
+def instance_inputs(ms, ids, seed):
+    """Packed f, g of the instances `ids` of a batch of sizes ms, with their
+    offsets (len(ids)+1 entries).  Instance i draws its entries (real and
+    imaginary parts uniform[-1, 1], f then g) from its own stream seeded by
+    (seed, i), so a share of the batch is generated alone with the values it
+    has in the whole batch."""
+    sub = [int(ms[i]) for i in ids]
+    off = np.zeros(len(sub) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sub)
+    f = np.empty(int(off[-1]), dtype=np.complex128)
+    g = np.empty(int(off[-1]), dtype=np.complex128)
+    for k, i in enumerate(ids):
+        r = np.random.Generator(np.random.PCG64([int(seed), int(i)]))
+        m = sub[k]
+        a, b = off[k], off[k + 1]
+        f[a:b] = r.uniform(-1.0, 1.0, m) + 1j * r.uniform(-1.0, 1.0, m)
+        g[a:b] = r.uniform(-1.0, 1.0, m) + 1j * r.uniform(-1.0, 1.0, m)
+    return f, g, off
 
 
 def batched_inputs(ms, seed):
