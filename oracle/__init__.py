@@ -38,6 +38,8 @@ from .conv import (  # noqa: F401
     conv_complex,
     conv_hermitian,
     conv_ternary_hermitian,
+    direct_complex_pq,
+    padded_complex_pq,
     dot_complex,
     dot_hermitian,
 )

@@ -295,6 +295,34 @@ def conv_ternary_hermitian(f, g, e):
 
 
 # ---------------------------------------------------------------------------
+# general padding (Sec. 2.4): p m data modes zero padded to N = q m
+# ---------------------------------------------------------------------------
+
+def direct_complex_pq(f, g, m, q, nout):
+    """h_k = sum_{j} F_j G_{(k - j) mod N}, k < nout, for F, G the inputs
+    (p m values each, p = len(f) / m) zero padded to N = q m: the cyclic
+    convolution that the zero-padded DFTs of size q m compute (the
+    definition the implicit p/q padding of Sec. 2.4 reproduces)."""
+    f, g = _c(f), _c(g)
+    N = q * m
+    F = np.zeros(N, dtype=np.complex128)
+    G = np.zeros(N, dtype=np.complex128)
+    F[: len(f)] = f
+    G[: len(g)] = g
+    h = np.zeros(nout, dtype=np.complex128)
+    for k in range(nout):
+        j = np.arange(len(f))
+        h[k] = np.sum(F[j] * G[(k - j) % N])
+    return h
+
+
+def padded_complex_pq(f, g, m, q, nout):
+    """Same result by the explicitly zero-padded FFT convolution of size N = q m."""
+    f, g = _c(f), _c(g)
+    return _padded_box([f, g], [[0], [0]], (q * m,), [0], (nout,))
+
+
+# ---------------------------------------------------------------------------
 # inputs as arrays of vectors (Sec. 3, 2D pseudospectral application): the
 # product f * g read as the dot product sum_i f_i * g_i of M pairs
 # ---------------------------------------------------------------------------
