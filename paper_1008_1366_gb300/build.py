@@ -17,13 +17,13 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdealias.so")
 
 SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu",
-           "partition.cu"]
+           "partition.cu", "pq.cu"]
 # the fixed-shape engine, one translation unit per precision
 FIXED = [(src, src.replace(".cu", f"_{tag}.o"), [f"-DDC_FX_P={ns}", f"-DDC_FX_C={c}"])
          for src in ("fixed_batched.cu", "fixed_axis.cu")
          for tag, ns, c in (("f", "f32", "float2"), ("d", "f64", "double2"))]
 # the fused 1D kernel, one translation unit per (kind, precision)
-INSTANCES = [(k, tag, c) for k in range(6) for tag, c in (("f", "float2"), ("d", "double2"))]
+INSTANCES = [(k, tag, c) for k in range(8) for tag, c in (("f", "float2"), ("d", "double2"))]
 
 
 def _units():
@@ -59,11 +59,25 @@ def _headers():
     return hs
 
 
+def _deps(obj, src, headers):
+    """The sources and in-tree headers an object was compiled from: the
+    dependency file nvcc wrote beside it (-MD), else every header."""
+    dfile = obj + ".d"
+    if not os.path.exists(dfile):
+        return [src] + headers
+    text = open(dfile).read().replace("\\\n", " ")
+    parts = text.split(":", 1)[1].split() if ":" in text else []
+    root = os.path.dirname(HERE)
+    deps = [os.path.abspath(p) for p in parts if os.path.abspath(p).startswith(root)]
+    return deps or [src] + headers
+
+
 def _stale(obj, src, headers):
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    return any(os.path.getmtime(p) > t for p in [src] + headers)
+    deps = _deps(obj, src, headers)
+    return any(not os.path.exists(p) or os.path.getmtime(p) > t for p in deps)
 
 
 def build(verbose=False, jobs=None, extra_flags=()):
@@ -78,7 +92,7 @@ def build(verbose=False, jobs=None, extra_flags=()):
         obj = os.path.join(BUILD, objname)
         if not _stale(obj, src, headers):
             return obj, ""
-        cmd = [nvcc] + ARCH + flags + defs + ["-I", INCLUDE, "-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + flags + defs + ["-I", INCLUDE, "-MD", "-MF", obj + ".d", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {objname}:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -86,8 +100,8 @@ def build(verbose=False, jobs=None, extra_flags=()):
 
     units = _units()
     jobs = jobs or min(len(units), os.cpu_count() or 4)
-    # longest units first
-    units.sort(key=lambda u: 0 if u[0] == "conv1d_inst.cu" else 1)
+    # longest units first: the fixed-shape engine, then the fused kernels
+    units.sort(key=lambda u: 0 if u[0] == "fixed_batched.cu" else (1 if u[0] == "conv1d_inst.cu" else 2))
     with ThreadPoolExecutor(max_workers=jobs) as ex:
         results = list(ex.map(compile_one, units))
     objs = [o for o, _ in results]
