@@ -26,10 +26,15 @@
  *   work and return; argument errors are detected on the host and returned
  *   synchronously, before anything is enqueued.  Errors found by kernels are
  *   recorded in the workspace status word, read with dc_read_status.
- * - Sizes: every transform length must be 2^a, 3*2^a or 5*2^a (including 1-5).
- *   Other sizes return DC_ERR_SIZE.  The first call for a new size builds that
- *   size's root tables with cudaMalloc and a generator kernel; to keep
- *   allocation out of a captured CUDA graph, call dc_prepare first.
+ * - Sizes: every transform length must be 2^a 3^b 5^c (any a, b, c >= 0; odd
+ *   Hermitian m = 2c+1 included, Sec. 2.3).  A length whose factors include
+ *   both 3 and 5 runs as direct DFTs up to 512, and above that when it splits
+ *   into two factors with one odd prime each (e.g. 720 = 20 x 36); lengths
+ *   without a plan, and lengths with another prime factor, return
+ *   DC_ERR_SIZE (dc_workspace_size reports which).  The first call for a new
+ *   size builds that size's root tables with cudaMalloc and a generator
+ *   kernel; to keep allocation out of a captured CUDA graph, call dc_prepare
+ *   first.
  * - Thread safety: calls may come from several host threads; table creation
  *   is serialized inside the library.
  */
@@ -46,7 +51,7 @@ extern "C" {
 typedef int32_t dc_status;
 #define DC_OK          0
 #define DC_ERR_ARG     1  /* null pointer, bad dtype/kind, negative size, bad overlap */
-#define DC_ERR_SIZE    2  /* size not 2^a, 3*2^a, 5*2^a; odd Hermitian m; too large */
+#define DC_ERR_SIZE    2  /* size not 2^a 3^b 5^c, without a plan, or too large */
 #define DC_ERR_ALIGN   3  /* pointer not aligned to its element size / workspace to 256 */
 #define DC_ERR_CUDA    4  /* a CUDA runtime call failed (dc_last_cuda_error gives it) */
 #define DC_ERR_TIMEOUT 5  /* a bounded device-side wait ran out (device status word) */
@@ -61,6 +66,8 @@ typedef int32_t dc_status;
 #define DC_KIND_TERNARY           2
 #define DC_KIND_COMPLEX_ADJOINT   3
 #define DC_KIND_HERMITIAN_ADJOINT 4
+#define DC_KIND_COMPLEX_DOT2      5  /* f1 * g1 + f2 * g2, complex (dc_conv_complex_dot2) */
+#define DC_KIND_HERMITIAN_DOT2    6  /* f1 * g1 + f2 * g2, centered Hermitian (dc_conv_hermitian_dot2) */
 
 /* Human-readable name of a status code (static string). */
 const char* dc_status_string(dc_status s);
@@ -118,6 +125,27 @@ dc_status dc_read_trace(const void* work, void* stream, uint64_t* out);
  * ------------------------------------------------------------------------- */
 dc_status dc_conv_complex_1d(const void* f, const void* g, void* h, int64_t m, int32_t dtype,
                              void* work, size_t work_bytes, void* stream);
+
+/* General implicit padding (Sec. 2.4): 1D complex convolution of f and g,
+ * each holding p m values (wavenumbers 0..pm-1), implicitly zero padded to
+ * N = q m.  The padded transform of size q m is computed as q transforms of
+ * size m of the p-term sums W_r(s) = sum_{t<p} zeta_{qm}^{r(tm+s)} U_{tm+s}
+ * (r < q), and the forward transform as q transforms of size m read at
+ * k mod m for every output.  Writes h_k = sum_j F_j G_{(k-j) mod qm},
+ * k = 0..nout-1, the cyclic convolution of the zero-padded inputs: for
+ * q >= 2p the outputs k < 2pm - 1 are the full linear convolution
+ * sum_{j} f_j g_{k-j} (p = 1, q = 2, nout = 2m - 1: all 2m - 1 outputs of the
+ * linear convolution of Sec. 2.1, of which dc_conv_complex_1d returns the
+ * first m) and the rest are zero; for q < 2p they wrap modulo qm.
+ * 1 <= p <= q <= 16, 1 <= nout <= q m; m of the form 2^a 3^b 5^c with a
+ * shared-memory transform (m up to several thousand), q m <= 2^24.  f, g:
+ * p m values, h: nout values; h may be f or g (in place) when that array
+ * holds nout values, no other overlap.  Workspace: dc_workspace_size_pq
+ * bytes.  DC_ERR_ARG for p, q or nout out of range; DC_ERR_SIZE for an m
+ * without such a transform. */
+dc_status dc_workspace_size_pq(int64_t m, int32_t p, int32_t q, int64_t nout, int32_t dtype, size_t* bytes);
+dc_status dc_conv_complex_1d_pq(const void* f, const void* g, void* h, int64_t m, int32_t p, int32_t q,
+                                int64_t nout, int32_t dtype, void* work, size_t work_bytes, void* stream);
 
 /* 1D centered Hermitian convolution under the 2/3 rule (Sec. 2.3, Function
  * conv; N = 3m).  f, g hold the wavenumbers 0..m-1 of Hermitian data
@@ -194,6 +222,20 @@ dc_status dc_conv_hermitian_2d(const void* f, const void* g, void* h, int64_t mx
 dc_status dc_conv_hermitian_3d(const void* f, const void* g, void* h, int64_t mx, int64_t my,
                                int64_t mz, int32_t dtype, void* work, size_t work_bytes,
                                void* stream);
+/* 2D and 3D centered Hermitian ternary convolutions (Sec. 4; Function tconv2
+ * and its 3D analogue): inputs f, g, e and output h of the Hermitian layout
+ * above; h_k = sum_{p+q+r=k} f_p g_q e_r over p, q, r in the box
+ * |p_d| <= m_d - 1 (componentwise), for the stored k.  Every axis is padded
+ * implicitly to N = 4m: the outer (centered) axes with the leading zero
+ * U_{-m} and two residues of 2m-point sub-transforms (Sec. 4.1, Procedures
+ * fft0tpadBackward / fft0tpadForward, Eqs. (fft0tbackward)-(fft0tforward)),
+ * the last axis by the 1D ternary rows (Sec. 4.2, Function tconv).  Inputs
+ * are projected on the last-axis-0 row / plane as for the binary case. */
+dc_status dc_conv_ternary_hermitian_2d(const void* f, const void* g, const void* e, void* h, int64_t mx,
+                                       int64_t my, int32_t dtype, void* work, size_t work_bytes, void* stream);
+dc_status dc_conv_ternary_hermitian_3d(const void* f, const void* g, const void* e, void* h, int64_t mx,
+                                       int64_t my, int64_t mz, int32_t dtype, void* work, size_t work_bytes,
+                                       void* stream);
 dc_status dc_conv_complex_2d_adjoint(const void* w, const void* f, const void* g, void* df,
                                      void* dg, int64_t mx, int64_t my, int32_t dtype, void* work,
                                      size_t work_bytes, void* stream);
@@ -206,6 +248,32 @@ dc_status dc_conv_hermitian_2d_adjoint(const void* w, const void* f, const void*
 dc_status dc_conv_hermitian_3d_adjoint(const void* w, const void* f, const void* g, void* df,
                                        void* dg, int64_t mx, int64_t my, int64_t mz, int32_t dtype,
                                        void* work, size_t work_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Inputs as arrays of vectors (Sec. 3, "2D pseudospectral application"): the
+ * product f * g read as the dot product of two pairs,
+ *   h = f1 * g1 + f2 * g2,
+ * with * the complex convolution (Functions cconv, cconv2, cconv3) or the
+ * centered Hermitian convolution (Functions conv, conv2 and the 3D
+ * analogue).  The two pointwise products are summed in physical space, so
+ * per residue one forward transform serves both pairs: five transforms per
+ * residue for the complex kind instead of six, and, with the real transforms
+ * of each Hermitian pair sharing one complex transform, three instead of
+ * four for the Hermitian kind.  The advective term of the 2D Euler equation,
+ * u . grad w, is dc_conv_hermitian_dot2 of (i k_x w, i k_y w) with
+ * (i k_y w / k^2, -i k_x w / k^2).
+ * ndim = 1, 2 or 3; dims: the unpadded sizes as for the single-pair calls;
+ * f1, g1, f2, g2, h: device arrays of the single-pair layout; h may be any
+ * of the inputs (in place); each Hermitian input is projected as for the
+ * single-pair call.  Workspace: dc_workspace_size with DC_KIND_*_DOT2 (3D:
+ * chunks follow the workspace as for the single-pair calls).
+ * ------------------------------------------------------------------------- */
+dc_status dc_conv_complex_dot2(int32_t ndim, const int64_t* dims, const void* f1, const void* g1,
+                               const void* f2, const void* g2, void* h, int32_t dtype, void* work,
+                               size_t work_bytes, void* stream);
+dc_status dc_conv_hermitian_dot2(int32_t ndim, const int64_t* dims, const void* f1, const void* g1,
+                                 const void* f2, const void* g2, void* h, int32_t dtype, void* work,
+                                 size_t work_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched 1D complex convolutions of uneven sizes in one persistent launch.

@@ -30,6 +30,12 @@ SIGNATURES = {
     "dc_conv_complex_1d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_hermitian_1d_adjoint": [_vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_complex_1d_noalloc": [_vp, _vp, _vp, _i64, _i32, _vp],
+    "dc_conv_complex_dot2": [_i32, ctypes.POINTER(_i64)] + [_vp] * 5 + [_i32, _vp, _sz, _vp],
+    "dc_conv_hermitian_dot2": [_i32, ctypes.POINTER(_i64)] + [_vp] * 5 + [_i32, _vp, _sz, _vp],
+    "dc_conv_ternary_hermitian_2d": [_vp, _vp, _vp, _vp, _i64, _i64, _i32, _vp, _sz, _vp],
+    "dc_conv_ternary_hermitian_3d": [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _i32, _vp, _sz, _vp],
+    "dc_workspace_size_pq": [_i64, _i32, _i32, _i64, _i32, ctypes.POINTER(_sz)],
+    "dc_conv_complex_1d_pq": [_vp, _vp, _vp, _i64, _i32, _i32, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_complex_2d": [_vp, _vp, _vp, _i64, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_complex_3d": [_vp, _vp, _vp, _i64, _i64, _i64, _i32, _vp, _sz, _vp],
     "dc_conv_hermitian_2d": [_vp, _vp, _vp, _i64, _i64, _i32, _vp, _sz, _vp],

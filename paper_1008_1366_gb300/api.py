@@ -14,7 +14,8 @@ import torch
 from . import _native
 
 C64, C128 = 0, 1
-KIND_COMPLEX, KIND_HERMITIAN, KIND_TERNARY, KIND_COMPLEX_ADJOINT, KIND_HERMITIAN_ADJOINT = range(5)
+(KIND_COMPLEX, KIND_HERMITIAN, KIND_TERNARY, KIND_COMPLEX_ADJOINT, KIND_HERMITIAN_ADJOINT,
+ KIND_COMPLEX_DOT2, KIND_HERMITIAN_DOT2) = range(7)
 PLAN_AUTOTUNE = 1
 PLAN_ONE_PER_LAUNCH = 4
 
@@ -133,6 +134,31 @@ def conv_complex_1d(f, g, out=None):
     return _run_1d("dc_conv_complex_1d", KIND_COMPLEX, [f, g], 1, None if out is None else [out])
 
 
+def conv_complex_1d_pq(f, g, m, p, q, nout=None):
+    """General implicit padding (dc_conv_complex_1d_pq): f, g hold p m values,
+    zero padded to q m; returns the nout first outputs of the padded cyclic
+    convolution (default: the full linear convolution, 2pm - 1 outputs, when
+    q >= 2p, else all q m)."""
+    dt = _inputs(f, g)
+    if f.dim() != 1 or f.shape[0] != p * m:
+        raise ValueError("inputs must be 1D of length p * m")
+    nout = int(nout) if nout is not None else (2 * p * m - 1 if q >= 2 * p else q * m)
+    out = torch.empty(nout, dtype=f.dtype, device=f.device)
+    ws = ctypes.c_size_t(0)
+    L = _native.lib()
+    check(L.dc_workspace_size_pq(m, p, q, nout, dt, ctypes.byref(ws)), "dc_workspace_size_pq")
+    work = _work(ws.value, f.device)
+    check(L.dc_conv_complex_1d_pq(_vp(f), _vp(g), _vp(out), m, p, q, nout, dt, _vp(work), ws.value, _stream(f)),
+          "dc_conv_complex_1d_pq")
+    return out
+
+
+def conv_complex_1d_full(f, g):
+    """All 2m - 1 outputs of the linear convolution of two length-m inputs
+    (general padding with p = 1, q = 2)."""
+    return conv_complex_1d_pq(f, g, f.shape[0], 1, 2)
+
+
 def conv_hermitian_1d(f, g, out=None):
     """Centered Hermitian 2/3-rule convolution (dc_conv_hermitian_1d)."""
     return _run_1d("dc_conv_hermitian_1d", KIND_HERMITIAN, [f, g], 1, None if out is None else [out])
@@ -182,6 +208,35 @@ def _run_md(name, kind, ins, nout, hermitian, slabs_per_chunk=None):
     return outs[0] if nout == 1 else tuple(outs)
 
 
+def _run_dot2(name, kind, ins, hermitian, slabs_per_chunk=None):
+    dt = _inputs(*ins)
+    if ins[0].dim() not in (1, 2, 3):
+        raise ValueError(f"{name}: expected 1D, 2D or 3D tensors")
+    dims = [ins[0].shape[0]] if ins[0].dim() == 1 else _dims(ins[0], hermitian)
+    out = torch.empty_like(ins[0])
+    if slabs_per_chunk is not None and len(dims) == 3:
+        ws = workspace_size_slabs(kind, dims, dt, slabs_per_chunk)
+    else:
+        ws = workspace_size(kind, dims, dt)
+    work = _work(ws, ins[0].device)
+    d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    fn = getattr(_native.lib(), name)
+    check(fn(len(dims), d, *[_vp(t) for t in ins], _vp(out), dt, _vp(work), ws, _stream(ins[0])), name)
+    return out
+
+
+def conv_complex_dot2(f1, g1, f2, g2, slabs_per_chunk=None):
+    """f1 * g1 + f2 * g2 for 1D/2D/3D complex convolutions with one forward
+    transform per residue for both pairs (dc_conv_complex_dot2)."""
+    return _run_dot2("dc_conv_complex_dot2", KIND_COMPLEX_DOT2, [f1, g1, f2, g2], False, slabs_per_chunk)
+
+
+def conv_hermitian_dot2(f1, g1, f2, g2, slabs_per_chunk=None):
+    """f1 * g1 + f2 * g2 for 1D/2D/3D centered Hermitian convolutions
+    (dc_conv_hermitian_dot2); e.g. the 2D Euler advective term."""
+    return _run_dot2("dc_conv_hermitian_dot2", KIND_HERMITIAN_DOT2, [f1, g1, f2, g2], True, slabs_per_chunk)
+
+
 # slabs_per_chunk (3D only): a workspace sized for chunks of at most that
 # many x-slabs (dc_workspace_size_slabs) instead of the default.
 
@@ -193,6 +248,11 @@ def conv_complex_nd(f, g, slabs_per_chunk=None):
 def conv_hermitian_nd(f, g, slabs_per_chunk=None):
     """2D/3D centered Hermitian convolution (dc_conv_hermitian_2d / _3d)."""
     return _run_md(f"dc_conv_hermitian_{f.dim()}d", KIND_HERMITIAN, [f, g], 1, True, slabs_per_chunk)
+
+
+def conv_ternary_hermitian_nd(f, g, e, slabs_per_chunk=None):
+    """2D/3D centered Hermitian ternary convolution (dc_conv_ternary_hermitian_2d / _3d)."""
+    return _run_md(f"dc_conv_ternary_hermitian_{f.dim()}d", KIND_TERNARY, [f, g, e], 1, True, slabs_per_chunk)
 
 
 def conv_complex_nd_adjoint(w, f, g, slabs_per_chunk=None):

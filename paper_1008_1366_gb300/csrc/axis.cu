@@ -13,8 +13,16 @@
 //   centered (q = 3): axis holds 2m-1 values, origin at m-1; residue
 //            r = -1, 0, 1 input w_{k,r} of Eqs. (2.4)-(2.5); forward Eq. (2.6)
 //            for k = -m+1..m-1.
-// Backward writes one array per residue, (outer, m, inner).  Forward reads the
-// q residue arrays and writes the recombined, scaled result.
+//   ternary  (q = 2, sub-transforms of length 2m, N = 4m; Sec. 4.1): axis
+//            holds 2m-1 values, origin at m-1, U_{-m} = 0; residue r = 0, 1
+//            backward u_{2l+r} = sum_k zeta_{2m}^{lk} zeta_{4m}^{rk} U_k, a
+//            2m-point transform of zeta_{4m}^{rk} U_k placed at k mod 2m;
+//            forward 4m U_k = sum_r zeta_{4m}^{-rk} sum_l zeta_{2m}^{-lk}
+//            u_{2l+r} for k = -m+1..m-1 (the transform read at k mod 2m;
+//            Eqs. (fft0tbackward)-(fft0tforward) before their index shift).
+// Backward writes one array per residue, (outer, L, inner) with L the
+// sub-transform length.  Forward reads the q residue arrays and writes the
+// recombined, scaled result.
 // Hermitian data: the self-conjugate subspace (last-axis wavenumber 0) is
 // projected onto U(-k) = conj U(k) while loading (Sec. 5 asks a routine to
 // enforce the symmetry); mode `dbl` instead forms U(k) + conj U(-k) there
@@ -64,19 +72,32 @@ __global__ void __launch_bounds__(512) axis_backward_kernel(AxisArgs a) {
   const int64_t i0 = (blockIdx.x - o * tiles_per_outer) * w;
   const int T = blockDim.x, tid = threadIdx.x;
   const C* tw = (const C*)a.tw;
-  const int q = a.centered ? 3 : 2;
+  const bool tern = a.centered == 2;
+  const int q = a.centered == 1 ? 3 : 2;
   const int nin = a.centered ? 2 * m - 1 : m;
+  const int L = axis_len(a.centered, m);
   const int cc = tid % w, ci = tid / w;
   const bool act = ci < a.p.tpt;
   using R = decltype(sm[0].x);
   for (int ri = 0; ri < q; ++ri) {
-    const int r = a.centered ? ri - 1 : ri;
-    for (int e = tid; e < m * w; e += T) {
+    const int r = a.centered == 1 ? ri - 1 : ri;
+    for (int e = tid; e < L * w; e += T) {
       const int k = e / w, c = e - k * w;
       const int64_t i = i0 + c;
       C v; v.x = 0; v.y = 0;
       if (i < a.inner) {
-        if (!a.centered) {
+        if (tern) {
+          // transform index k holds wavenumber k (k < m) or k - 2m (k > m);
+          // k = m is the zero U_{-m}
+          const int kw = k < m ? k : k - 2 * m;
+          if (k != m) {
+            v = load_sym(a, in, o, nin, kw + m - 1, i, dbl);
+            if (r && kw) {
+              const C t = __ldg(&tw[kw > 0 ? kw : -kw]);   // zeta_{4m}^{|k|}
+              v = kw > 0 ? cmul(v, t) : cmulc(v, t);
+            }
+          }
+        } else if (!a.centered) {
           v = load_sym(a, in, o, nin, k, i, dbl);
           if (r) v = cmul(v, __ldg(&tw[k]));
         } else {
@@ -100,10 +121,10 @@ __global__ void __launch_bounds__(512) axis_backward_kernel(AxisArgs a) {
     __syncthreads();
     fft_smem<1>(sm + cc, w, a.p, ci, act, tw, a.TN);
     C* out = (C*)a.out[z * 3 + ri];
-    for (int e = tid; e < m * w; e += T) {
+    for (int e = tid; e < L * w; e += T) {
       const int k = e / w, c = e - k * w;
       const int64_t i = i0 + c;
-      if (i < a.inner) out[(o * m + k) * a.inner + i] = sm[e];
+      if (i < a.inner) out[(o * L + k) * a.inner + i] = sm[e];
     }
     __syncthreads();
   }
@@ -116,24 +137,26 @@ __global__ void __launch_bounds__(512) axis_forward_kernel(AxisArgs a) {
   const int z = blockIdx.y;
   const int w = a.w, m = a.m;
   const int nout = a.centered ? 2 * m - 1 : m;
-  C* H = sm + (size_t)m * w;
+  const bool tern = a.centered == 2;
+  const int L = axis_len(a.centered, m);
+  C* H = sm + (size_t)L * w;
   const int64_t tiles_per_outer = (a.inner + w - 1) / w;
   const int64_t o = blockIdx.x / tiles_per_outer;
   const int64_t i0 = (blockIdx.x - o * tiles_per_outer) * w;
   const int T = blockDim.x, tid = threadIdx.x;
   const C* tw = (const C*)a.tw;
-  const int q = a.centered ? 3 : 2;
+  const int q = a.centered == 1 ? 3 : 2;
   const int cc = tid % w, ci = tid / w;
   const bool act = ci < a.p.tpt;
   using R = decltype(sm[0].x);
   for (int ri = 0; ri < q; ++ri) {
-    const int r = a.centered ? ri - 1 : ri;
+    const int r = a.centered == 1 ? ri - 1 : ri;
     const C* src = (const C*)a.fin[z * 3 + ri];
-    for (int e = tid; e < m * w; e += T) {
+    for (int e = tid; e < L * w; e += T) {
       const int k = e / w, c = e - k * w;
       const int64_t i = i0 + c;
       C v; v.x = 0; v.y = 0;
-      if (i < a.inner) v = src[(o * m + k) * a.inner + i];
+      if (i < a.inner) v = src[(o * L + k) * a.inner + i];
       sm[e] = v;
     }
     __syncthreads();
@@ -141,7 +164,7 @@ __global__ void __launch_bounds__(512) axis_forward_kernel(AxisArgs a) {
     for (int e = tid; e < nout * w; e += T) {
       const int j = e / w, c = e - j * w;
       const int k = a.centered ? j - (m - 1) : j;       // wavenumber of output row j
-      const int kk = k < 0 ? k + m : k;                  // index of the m-periodic sub-transform
+      const int kk = k < 0 ? k + L : k;                  // index of the L-periodic sub-transform
       C x = sm[kk * w + c];
       if (r != 0) {
         // zeta_{qm}^{-rk}
@@ -155,7 +178,7 @@ __global__ void __launch_bounds__(512) axis_forward_kernel(AxisArgs a) {
     __syncthreads();
   }
   C* out = (C*)a.fout[z];
-  const R scale = (R)1 / (R)(q * m);
+  const R scale = (R)1 / (R)(tern ? 4 * m : q * m);
   const bool halve = (a.halve_mask >> z) & 1;
   for (int e = tid; e < nout * w; e += T) {
     const int j = e / w, c = e - j * w;

@@ -170,7 +170,8 @@ dc_status run_md(int32_t pk, int ndim, const int64_t* dims, const void* const* i
   const int ds = dsize_of(dtype);
   if (!ds) return DC_ERR_ARG;
   for (int d = 0; d < ndim; ++d) if (dims[d] < 1) return DC_ERR_ARG;
-  const bool herm = pk == DC_KIND_HERMITIAN || pk == DC_KIND_HERMITIAN_ADJOINT;
+  const bool herm = pk == DC_KIND_HERMITIAN || pk == DC_KIND_HERMITIAN_ADJOINT || pk == DC_KIND_HERMITIAN_DOT2 ||
+                    pk == DC_KIND_TERNARY;
   int64_t n = 1;
   for (int d = 0; d < ndim; ++d) n *= (herm && d < ndim - 1) ? 2 * dims[d] - 1 : dims[d];
   dc_status st = check_ptrs(ins, nin, outs, nout, (size_t)n * ds, ds);
@@ -187,6 +188,8 @@ int kind_of_public(int32_t k) {
     case DC_KIND_TERNARY: return K_TERNARY;
     case DC_KIND_COMPLEX_ADJOINT: return K_COMPLEX_ADJ;
     case DC_KIND_HERMITIAN_ADJOINT: return K_HERMITIAN_ADJ;
+    case DC_KIND_COMPLEX_DOT2: return K_COMPLEX_DOT2;
+    case DC_KIND_HERMITIAN_DOT2: return K_HERMITIAN_DOT2;
   }
   return -1;
 }
@@ -307,6 +310,75 @@ dc_status dc_conv_hermitian_1d_adjoint(const void* w, const void* f, const void*
   const void* ins[3] = {w, f, g};
   void* outs[2] = {df, dg};
   return run_1d(K_HERMITIAN_ADJ, ins, 3, outs, 2, m, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_workspace_size_pq(int64_t m, int32_t p, int32_t q, int64_t nout, int32_t dtype, size_t* bytes) {
+  const int ds = dsize_of(dtype);
+  if (!ds || !bytes) return DC_ERR_ARG;
+  FftPlan plan;
+  return pq_plan(m, p, q, nout, ds, &plan, bytes);
+}
+
+dc_status dc_conv_complex_1d_pq(const void* f, const void* g, void* h, int64_t m, int32_t p, int32_t q,
+                                int64_t nout, int32_t dtype, void* work, size_t work_bytes, void* stream) {
+  const int ds = dsize_of(dtype);
+  if (!ds || m < 1 || p < 1 || nout < 1) return DC_ERR_ARG;
+  // inputs hold p m values, the output nout; h may be f or g, no other overlap
+  if (!f || !g || !h) return DC_ERR_ARG;
+  if (!aligned(f, ds) || !aligned(g, ds) || !aligned(h, ds)) return DC_ERR_ALIGN;
+  const size_t in_bytes = (size_t)p * m * ds, out_bytes = (size_t)nout * ds;
+  for (const void* x : {f, g}) {
+    const char* a = (const char*)h;
+    const char* b = (const char*)x;
+    if (x != h && a < b + in_bytes && b < a + out_bytes) return DC_ERR_ARG;
+  }
+  dc_status st = DC_OK;
+  FftPlan plan;
+  size_t need = 0;
+  if ((st = pq_plan(m, p, q, nout, ds, &plan, &need)) != DC_OK) return st;
+  if ((st = check_work(work, work_bytes, need)) != DC_OK) return st;
+  return pq_run(f, g, h, m, p, q, nout, ds, work, work_bytes, (cudaStream_t)stream);
+}
+
+static dc_status run_dot2(int32_t pk, int kind, int32_t ndim, const int64_t* dims, const void* f1,
+                          const void* g1, const void* f2, const void* g2, void* h, int32_t dtype, void* work,
+                          size_t work_bytes, void* stream) {
+  if (!dims || ndim < 1 || ndim > 3) return DC_ERR_ARG;
+  const void* ins[4] = {f1, g1, f2, g2};
+  void* outs[1] = {h};
+  if (ndim == 1) return run_1d(kind, ins, 4, outs, 1, dims[0], dtype, work, work_bytes, stream);
+  return run_md(pk, ndim, dims, ins, 4, outs, 1, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_complex_dot2(int32_t ndim, const int64_t* dims, const void* f1, const void* g1,
+                               const void* f2, const void* g2, void* h, int32_t dtype, void* work,
+                               size_t work_bytes, void* stream) {
+  return run_dot2(DC_KIND_COMPLEX_DOT2, K_COMPLEX_DOT2, ndim, dims, f1, g1, f2, g2, h, dtype, work, work_bytes,
+                  stream);
+}
+
+dc_status dc_conv_hermitian_dot2(int32_t ndim, const int64_t* dims, const void* f1, const void* g1,
+                                 const void* f2, const void* g2, void* h, int32_t dtype, void* work,
+                                 size_t work_bytes, void* stream) {
+  return run_dot2(DC_KIND_HERMITIAN_DOT2, K_HERMITIAN_DOT2, ndim, dims, f1, g1, f2, g2, h, dtype, work,
+                  work_bytes, stream);
+}
+
+dc_status dc_conv_ternary_hermitian_2d(const void* f, const void* g, const void* e, void* h, int64_t mx,
+                                       int64_t my, int32_t dtype, void* work, size_t work_bytes, void* stream) {
+  const void* ins[3] = {f, g, e};
+  void* outs[1] = {h};
+  const int64_t d[2] = {mx, my};
+  return run_md(DC_KIND_TERNARY, 2, d, ins, 3, outs, 1, dtype, work, work_bytes, stream);
+}
+
+dc_status dc_conv_ternary_hermitian_3d(const void* f, const void* g, const void* e, void* h, int64_t mx,
+                                       int64_t my, int64_t mz, int32_t dtype, void* work, size_t work_bytes,
+                                       void* stream) {
+  const void* ins[3] = {f, g, e};
+  void* outs[1] = {h};
+  const int64_t d[3] = {mx, my, mz};
+  return run_md(DC_KIND_TERNARY, 3, d, ins, 3, outs, 1, dtype, work, work_bytes, stream);
 }
 
 dc_status dc_conv_complex_2d(const void* f, const void* g, void* h, int64_t mx, int64_t my,

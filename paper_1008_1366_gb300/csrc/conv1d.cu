@@ -16,6 +16,8 @@ DC_DECL(2)
 DC_DECL(3)
 DC_DECL(4)
 DC_DECL(5)
+DC_DECL(6)
+DC_DECL(7)
 #undef DC_DECL
 
 dc_status launch_conv1d(int kind, int dsize, const ConvArgs& a, int grid, int smem, cudaStream_t s) {
@@ -27,6 +29,8 @@ dc_status launch_conv1d(int kind, int dsize, const ConvArgs& a, int grid, int sm
     case 3: return f ? conv1d_launch_3_f(a, grid, smem, s) : conv1d_launch_3_d(a, grid, smem, s);
     case 4: return f ? conv1d_launch_4_f(a, grid, smem, s) : conv1d_launch_4_d(a, grid, smem, s);
     case 5: return f ? conv1d_launch_5_f(a, grid, smem, s) : conv1d_launch_5_d(a, grid, smem, s);
+    case 6: return f ? conv1d_launch_6_f(a, grid, smem, s) : conv1d_launch_6_d(a, grid, smem, s);
+    case 7: return f ? conv1d_launch_7_f(a, grid, smem, s) : conv1d_launch_7_d(a, grid, smem, s);
   }
   return DC_ERR_ARG;
 }
@@ -40,6 +44,8 @@ dc_status conv1d_blocks_per_sm(int kind, int dsize, int smem, int* out) {
     case 3: return f ? conv1d_occupancy_3_f(smem, out) : conv1d_occupancy_3_d(smem, out);
     case 4: return f ? conv1d_occupancy_4_f(smem, out) : conv1d_occupancy_4_d(smem, out);
     case 5: return f ? conv1d_occupancy_5_f(smem, out) : conv1d_occupancy_5_d(smem, out);
+    case 6: return f ? conv1d_occupancy_6_f(smem, out) : conv1d_occupancy_6_d(smem, out);
+    case 7: return f ? conv1d_occupancy_7_f(smem, out) : conv1d_occupancy_7_d(smem, out);
   }
   return DC_ERR_ARG;
 }

@@ -28,7 +28,7 @@ namespace dc {
 constexpr int kThreads = 512;
 
 struct ConvArgs {
-  const void* in[3];      // inputs (f, g, e) or (w, f, g) for gradients
+  const void* in[4];      // inputs (f, g, e), (w, f, g) for gradients, (f1, g1, f2, g2) for dot products
   void* out[2];           // outputs (h) or (df, dg)
   const int64_t* off;     // per-instance element offsets (device) or null: inst * stride
   int64_t stride;
@@ -53,15 +53,16 @@ template <class C> struct Ctx {
   const C* in0;     // inputs and outputs as named pointers: never indexed at
   const C* in1;     // run time, so they stay in registers
   const C* in2;
+  const C* in3;
   C* out0;
   C* out1;
   int m, TN;
   Roots<C> rt;
 };
 
-// input x of an instance (x = 0, 1, 2)
+// input x of an instance (x = 0, 1, 2, 3)
 template <class C> __device__ __forceinline__ const C* in_ptr(const Ctx<C>& c, int x) {
-  return x == 0 ? c.in0 : (x == 1 ? c.in1 : c.in2);
+  return x == 0 ? c.in0 : (x == 1 ? c.in1 : (x == 2 ? c.in2 : c.in3));
 }
 
 // ---------------------------------------------------------------------------
@@ -237,6 +238,47 @@ template <class C> struct KP<K_HERMITIAN_PAIR, C> {
   __device__ static C finish(int o, C a, int k, int m) { return KP<K_HERMITIAN, C>::finish(o, a, k, m); }
 };
 
+// Inputs as arrays of vectors (Sec. 3, 2D pseudospectral application): the
+// product f * g read as the dot product f1 * g1 + f2 * g2 of two pairs.  The
+// four inputs take one backward transform each per residue (Eq. (2.1)); the
+// two pointwise products are summed in physical space, so one forward
+// transform per residue (Eq. (2.2)) serves both pairs: five transforms per
+// residue instead of six.
+template <class C> struct KP<K_COMPLEX_DOT2, C> {
+  static constexpr int Q = 2, NARR = 4, NFWD = 1;
+  __device__ static C build(const Ctx<C>& c, int x, int k, int ri, int m, const Roots<C>& rt) {
+    return KP<K_COMPLEX, C>::build(c, x, k, ri, m, rt);
+  }
+  __device__ static void pointwise(C* v) { v[0] = cadd(cmul(v[0], v[1]), cmul(v[2], v[3])); }
+  __device__ static C contrib(int o, C X, int k, int ri, int m, const Roots<C>& rt) {
+    return KP<K_COMPLEX, C>::contrib(o, X, k, ri, m, rt);
+  }
+  __device__ static C finish(int o, C a, int k, int m) { return KP<K_COMPLEX, C>::finish(o, a, k, m); }
+};
+
+// The centered Hermitian dot product of two pairs (same passage, Sec. 2.3):
+// each pair's real backward transforms share one complex transform of
+// w^f + i w^g, so the two real products need two backward transforms and
+// their sum one forward transform per residue (three, against four for two
+// separate convolutions).
+template <class C> struct KP<K_HERMITIAN_DOT2, C> {
+  static constexpr int Q = 3, NARR = 2, NFWD = 1;
+  __device__ static C build(const Ctx<C>& c, int x, int k, int ri, int m, const Roots<C>& rt) {
+    const int r = ri - 1;
+    const C* a = x ? c.in2 : c.in0;
+    const C* b = x ? c.in3 : c.in1;
+    return pack_i(herm_w(a, k, r, m, rt, real_part(a[0])), herm_w(b, k, r, m, rt, real_part(b[0])));
+  }
+  __device__ static void pointwise(C* v) {
+    v[0].x = v[0].x * v[0].y + v[1].x * v[1].y;
+    v[0].y = 0;
+  }
+  __device__ static C contrib(int o, C X, int k, int ri, int m, const Roots<C>& rt) {
+    return KP<K_HERMITIAN, C>::contrib(o, X, k, ri, m, rt);
+  }
+  __device__ static C finish(int o, C a, int k, int m) { return KP<K_HERMITIAN, C>::finish(o, a, k, m); }
+};
+
 // ---------------------------------------------------------------------------
 // stage interpreter.  Every transform stage of every path is one call of
 // stage_call (or boundary_call for the stage that meets the product), with
@@ -351,7 +393,8 @@ __device__ __forceinline__ void stage_r(int Ns, int L, int tpt, int sgn, Src<C> 
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = i + b * tpt;
-      const int k = j & (Ns - 1);   // Ns is a power of two (odd radix last)
+      // Ns is a power of two up to the first odd radix (the odd radices come last)
+      const int k = (Ns & (Ns - 1)) ? j % Ns : j & (Ns - 1);
       const int ob = (j - k) * RR + k;
 #pragma unroll
       for (int q = 0; q < RR; ++q) {
@@ -571,6 +614,7 @@ template <class C> __device__ __forceinline__ Ctx<C> inst_ctx(const ConvArgs& a,
   c.in0 = a.in[0] ? (const C*)a.in[0] + off : nullptr;
   c.in1 = a.in[1] ? (const C*)a.in[1] + off : nullptr;
   c.in2 = a.in[2] ? (const C*)a.in[2] + off : nullptr;
+  c.in3 = a.in[3] ? (const C*)a.in[3] + off : nullptr;
   c.out0 = a.out[0] ? (C*)a.out[0] + off : nullptr;
   c.out1 = a.out[1] ? (C*)a.out[1] + off : nullptr;
   c.m = m;

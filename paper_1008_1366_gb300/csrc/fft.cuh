@@ -205,9 +205,11 @@ __device__ __noinline__ void fft_smem(C* base, int es, const FftPlan& p, int i, 
     case 8:  fft_run<8, S>(base, es, p, i, active, tw, TN); break;
     case 10: fft_run<10, S>(base, es, p, i, active, tw, TN); break;
     case 12: fft_run<12, S>(base, es, p, i, active, tw, TN); break;
+    case 15: fft_run<15, S>(base, es, p, i, active, tw, TN); break;   // lengths with factors 3 and 5
     case 16: if constexpr (sizeof(C) == 8) fft_run<16, S>(base, es, p, i, active, tw, TN); break;
     case 20: if constexpr (sizeof(C) == 8) fft_run<20, S>(base, es, p, i, active, tw, TN); break;
     case 24: if constexpr (sizeof(C) == 8) fft_run<24, S>(base, es, p, i, active, tw, TN); break;
+    case 30: if constexpr (sizeof(C) == 8) fft_run<30, S>(base, es, p, i, active, tw, TN); break;
     default: break;   // E = 1: length-1 transform, nothing to do
   }
 }

@@ -123,7 +123,9 @@ __device__ __forceinline__ void bfly(C* v, int i, int tpt, int Ns, int tstr, con
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if (Ns > 1) {
-      const int e = ((i + b * tpt) & (Ns - 1)) * tstr;   // Ns is a power of two
+      // Ns is a power of two up to the first odd radix (the odd radices come last)
+      const int j = i + b * tpt;
+      const int e = ((Ns & (Ns - 1)) ? j % Ns : j & (Ns - 1)) * tstr;
 #pragma unroll
       for (int q = 1; q < R; ++q) {
         C w = rt.at(q * e);

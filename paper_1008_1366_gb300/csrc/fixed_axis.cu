@@ -306,6 +306,7 @@ dc_status launch_L(bool forward, const AxisArgs& a, int narrays, cudaStream_t s)
 
 // DC_ERR_SIZE when the axis length is not one this file compiles
 dc_status launch_axis_fixed(bool forward, const AxisArgs& a, int narrays, cudaStream_t s) {
+  if (a.centered == 2) return DC_ERR_SIZE;   // ternary axes: the runtime-shaped kernels (axis.cu)
   switch (a.m) {
     case 64: return launch_L<64>(forward, a, narrays, s);
     case 128: return launch_L<128>(forward, a, narrays, s);

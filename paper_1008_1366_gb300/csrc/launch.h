@@ -45,4 +45,11 @@ dc_status fx_ternary_run(int64_t m, int ds, const void* f, const void* g, const 
                          size_t work_bytes, cudaStream_t s);
 dc_status conv1d_blocks_per_sm(int kind, int dsize, int smem, int* out);
 
+// general implicit padding (pq.cu): checks and plans a call (the m-point
+// transform, the workspace bytes), and runs it
+struct FftPlan;
+dc_status pq_plan(int64_t m, int32_t p, int32_t q, int64_t nout, int ds, FftPlan* plan_out, size_t* work);
+dc_status pq_run(const void* f, const void* g, void* h, int64_t m, int32_t p, int32_t q, int64_t nout, int ds,
+                 void* work, size_t work_bytes, cudaStream_t s);
+
 }  // namespace dc

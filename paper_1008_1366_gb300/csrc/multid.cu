@@ -48,7 +48,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Md {
   int pk = 0, ndim = 0, ds = 0;
   int64_t m[3] = {0, 0, 0};
-  bool herm = false, adj = false;
+  bool herm = false, adj = false, tern = false;
+  int64_t Lx = 0, Ly = 0;     // sub-transform lengths of the outer axes (m, or 2m for ternary)
   int qa = 2, narr = 2, nout = 1, row_kind = K_COMPLEX;
   int64_t ny_in = 0;          // stored y extent (3D): my or 2my-1
   int64_t nx = 0;             // elements of one x-level residue array
@@ -66,21 +67,23 @@ struct Md {
 
 int smem_cap() { return device_info().smem_optin - kStaticSmemReserve; }
 
-bool axis_cfg(bool centered, int64_t m, int ds, bool with_table, AxisArgs* a) {
-  const int emax = ds == 8 ? 24 : 12;
+// mode: 0 complex, 1 centered (q = 3), 2 centered ternary (q = 2, length 2m)
+bool axis_cfg(int mode, int64_t m, int ds, bool with_table, AxisArgs* a) {
+  const int emax = ds == 8 ? 30 : 15;
   FftPlan p;
-  if (m < 1 || m > (1 << 16) || !make_fft_plan((int)m, emax, &p)) return false;
+  const int64_t L = mode == 2 ? 2 * m : m;
+  if (m < 1 || L > (1 << 16) || !make_fft_plan((int)L, emax, &p)) return false;
   if (p.tpt > 512) return false;
-  const int colb = axis_smem(true, centered, (int)m, 1, ds);
+  const int colb = axis_smem(true, mode, (int)m, 1, ds);
   int w = 1;
   while (w * 2 <= 32 && (w * 2) * p.tpt <= 512 && (w * 2) * colb <= smem_cap()) w *= 2;
   if (colb > smem_cap()) return false;
   *a = AxisArgs{};
   a->m = (int32_t)m;
-  a->centered = centered ? 1 : 0;
+  a->centered = mode;
   a->w = w;
   a->p = p;
-  a->TN = (int32_t)((centered ? 3 : 2) * m);
+  a->TN = (int32_t)((mode == 2 ? 4 : mode == 1 ? 3 : 2) * m);
   if (with_table) {
     const void* tw = nullptr;
     if (get_root_table(a->TN, ds, &tw) != DC_OK) return false;
@@ -99,30 +102,39 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
     md->m[d] = dims[d];
   }
   md->pk = pk; md->ndim = ndim; md->ds = ds;
-  md->herm = pk == DC_KIND_HERMITIAN || pk == DC_KIND_HERMITIAN_ADJOINT;
+  const bool dot = pk == DC_KIND_COMPLEX_DOT2 || pk == DC_KIND_HERMITIAN_DOT2;
+  md->tern = pk == DC_KIND_TERNARY;
+  md->herm = pk == DC_KIND_HERMITIAN || pk == DC_KIND_HERMITIAN_ADJOINT || pk == DC_KIND_HERMITIAN_DOT2 || md->tern;
   md->adj = pk == DC_KIND_COMPLEX_ADJOINT || pk == DC_KIND_HERMITIAN_ADJOINT;
-  if (pk == DC_KIND_TERNARY || pk < 0 || pk > 4) return DC_ERR_ARG;
-  md->qa = md->herm ? 3 : 2;
-  md->narr = md->adj ? 3 : 2;
+  if (pk < 0 || pk > DC_KIND_HERMITIAN_DOT2) return DC_ERR_ARG;
+  md->qa = md->tern ? 2 : (md->herm ? 3 : 2);
+  md->narr = dot ? 4 : (md->adj || md->tern ? 3 : 2);
   md->nout = md->adj ? 2 : 1;
-  md->row_kind = md->herm ? (md->adj ? K_HERMITIAN_PAIR : K_HERMITIAN)
-                          : (md->adj ? K_COMPLEX_ADJ : K_COMPLEX);
+  md->row_kind = md->tern ? K_TERNARY
+                 : dot ? (md->herm ? K_HERMITIAN_DOT2 : K_COMPLEX_DOT2)
+                       : md->herm ? (md->adj ? K_HERMITIAN_PAIR : K_HERMITIAN)
+                                  : (md->adj ? K_COMPLEX_ADJ : K_COMPLEX);
+  // outer axes: centered for Hermitian data, of twice the length for the
+  // ternary kind (N = 4m per axis, Sec. 4.1)
+  const int amode = md->tern ? 2 : (md->herm ? 1 : 0);
   const int64_t mx = md->m[0], my = md->m[1], mlast = md->m[ndim - 1];
-  if (!axis_cfg(md->herm, mx, ds, with_tables, &md->ax)) return DC_ERR_SIZE;
+  md->Lx = axis_len(amode, (int)mx);
+  md->Ly = ndim == 3 ? axis_len(amode, (int)my) : 0;
+  if (!axis_cfg(amode, mx, ds, with_tables, &md->ax)) return DC_ERR_SIZE;
   int64_t nrows;   // rows of the row kernel per launch
   if (ndim == 2) {
-    md->nx = mx * my;
-    nrows = md->qa * mx;
+    md->nx = md->Lx * my;
+    nrows = md->qa * md->Lx;
   } else {
-    if (!axis_cfg(md->herm, my, ds, with_tables, &md->ay)) return DC_ERR_SIZE;
+    if (!axis_cfg(amode, my, ds, with_tables, &md->ay)) return DC_ERR_SIZE;
     md->ny_in = md->herm ? 2 * my - 1 : my;
-    md->nx = mx * md->ny_in * mlast;
-    md->slabs = md->qa * mx;
+    md->nx = md->Lx * md->ny_in * mlast;
+    md->slabs = md->qa * md->Lx;
     md->sx = md->ny_in * mlast;
-    const size_t per_slab = (size_t)md->narr * md->qa * my * mlast * ds;
+    const size_t per_slab = (size_t)md->narr * md->qa * md->Ly * mlast * ds;
     md->S = std::max<int64_t>(1, std::min<int64_t>(md->slabs, kChunkBudget / per_slab));
     if (slabs_req > 0) md->S = std::min<int64_t>(slabs_req, md->slabs);
-    nrows = md->qa * md->S * my;
+    nrows = md->qa * md->S * md->Ly;
   }
   if (!make_cfg(md->row_kind, mlast, ds, kThreads, smem_cap(), 0, &md->rows)) return DC_ERR_SIZE;
   if (with_tables) {
@@ -142,14 +154,14 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   md->rows_slot = align_up(cfg_scratch_bytes(md->row_kind, md->rows, ds), 256);
   size_t off = kHeader + align_up((size_t)md->narr * md->qa * md->nx * ds, 256);
   md->off_y = off;
-  if (ndim == 3) off += align_up((size_t)md->narr * md->qa * md->S * my * mlast * ds, 256);
+  if (ndim == 3) off += align_up((size_t)md->narr * md->qa * md->S * md->Ly * mlast * ds, 256);
   md->off_rows = off;
   size_t rows_bytes = (size_t)md->rows_grid * md->rows_slot;
   // binary complex and centered Hermitian rows of a size in the set, and
   // the gradient pair rows of a one-level size, run on the fixed-shape
   // engine
   md->rows_n[0] = nrows;
-  md->rows_n[1] = ndim == 3 && md->slabs % md->S ? md->qa * (md->slabs % md->S) * my : nrows;
+  md->rows_n[1] = ndim == 3 && md->slabs % md->S ? md->qa * (md->slabs % md->S) * md->Ly : nrows;
   // The gradient pair transforms W alone and keeps the real part of its
   // transform, which drops any non-Hermitian rounding of W's rows (two
   // plain convolutions with W packed beside g would carry it into g's
@@ -187,7 +199,7 @@ dc_status run_rows(const Md& md, const void* const* in, void* const* out, int64_
     return dc_conv_complex_1d_batched(p, in[0], in[1], out[0], rw, rb, s);
   }
   ConvArgs a{};
-  for (int x = 0; x < 3; ++x) a.in[x] = in[x];
+  for (int x = 0; x < 4; ++x) a.in[x] = in[x];
   for (int o = 0; o < 2; ++o) a.out[o] = out[o];
   a.stride = md.m[md.ndim - 1];
   a.ninst = (int32_t)nrows;
@@ -294,16 +306,16 @@ dc_status md_run(int pk, int ndim, const int64_t* dims, int ds, const void* cons
   if ((st = launch_axis(false, ds, ax, md.narr, s)) != DC_OK) return st;
 
   if (md.ndim == 2) {
-    const void* rin[3] = {nullptr, nullptr, nullptr};
+    const void* rin[4] = {nullptr, nullptr, nullptr, nullptr};
     void* rout[2] = {nullptr, nullptr};
     for (int z = 0; z < md.narr; ++z) rin[z] = xres(z, 0);
     for (int o = 0; o < md.nout; ++o) rout[o] = xres(oslot0 + o, 0);
-    if ((st = run_rows(md, rin, rout, (int64_t)qa * mx, wk, s)) != DC_OK) return st;
+    if ((st = run_rows(md, rin, rout, (int64_t)qa * md.Lx, wk, s)) != DC_OK) return st;
   } else {
     char* Y = wk + md.off_y;
     for (int64_t s0 = 0; s0 < md.slabs; s0 += md.S) {
       const int64_t Sc = std::min<int64_t>(md.S, md.slabs - s0);
-      const size_t ych = (size_t)Sc * my * mz;   // elements of one y-level residue array
+      const size_t ych = (size_t)Sc * md.Ly * mz;   // elements of one y-level residue array
       auto yres = [&](int z, int r) { return (void*)(Y + ((size_t)z * qa + r) * ych * ds); };
       AxisArgs ay = md.ay;
       ay.outer = Sc;
@@ -313,11 +325,11 @@ dc_status md_run(int pk, int ndim, const int64_t* dims, int ds, const void* cons
         for (int r = 0; r < qa; ++r) ay.out[z * 3 + r] = yres(z, r);
       }
       if ((st = launch_axis(false, ds, ay, md.narr, s)) != DC_OK) return st;
-      const void* rin[3] = {nullptr, nullptr, nullptr};
+      const void* rin[4] = {nullptr, nullptr, nullptr, nullptr};
       void* rout[2] = {nullptr, nullptr};
       for (int z = 0; z < md.narr; ++z) rin[z] = yres(z, 0);
       for (int o = 0; o < md.nout; ++o) rout[o] = yres(oslot0 + o, 0);
-      if ((st = run_rows(md, rin, rout, (int64_t)qa * Sc * my, wk, s)) != DC_OK) return st;
+      if ((st = run_rows(md, rin, rout, (int64_t)qa * Sc * md.Ly, wk, s)) != DC_OK) return st;
       AxisArgs yf = md.ay;
       yf.outer = Sc;
       yf.inner = mz;

@@ -11,14 +11,14 @@
 namespace dc {
 
 struct AxisArgs {
-  const void* in[3];      // backward: arrays to transform (blockIdx.y selects)
-  void* out[9];           // backward: out[array * 3 + residue], layout (outer, m, inner)
+  const void* in[4];      // backward: arrays to transform (blockIdx.y selects)
+  void* out[12];          // backward: out[array * 3 + residue], layout (outer, m, inner)
   const void* fin[9];     // forward: fin[output * 3 + residue], layout (outer, m, inner)
   void* fout[3];          // forward: outputs, layout (outer, m or 2m-1, inner)
   int64_t outer, inner;
   int64_t proj_mz, proj_ny;   // 3D self-conjugate plane geometry (inner = proj_ny * proj_mz)
   int32_t m;              // unpadded size along the axis
-  int32_t centered;       // 0: complex q = 2; 1: centered q = 3
+  int32_t centered;       // 0: complex q = 2; 1: centered q = 3; 2: centered ternary q = 2 of length 2m
   int32_t proj;           // 0: none; 2: 2D column ky = 0; 3: 3D plane kz = 0
   int32_t w;              // columns per block
   int32_t dbl_mask;       // backward arrays whose self-conjugate subspace is U(k) + conj U(-k)
@@ -28,9 +28,12 @@ struct AxisArgs {
   FftPlan p;              // length-m sub-transform plan
 };
 
+// length of the sub-transforms of an axis of unpadded size m
+__host__ __device__ inline int axis_len(int centered, int m) { return centered == 2 ? 2 * m : m; }
 inline int axis_smem(bool forward, int centered, int m, int w, int ds) {
   const int nout = centered ? 2 * m - 1 : m;
-  return (forward ? (m + nout) : m) * w * ds;
+  const int L = axis_len(centered, m);
+  return (forward ? (L + nout) : L) * w * ds;
 }
 
 dc_status launch_axis(bool forward, int dsize, const AxisArgs& a, int narrays, cudaStream_t s);

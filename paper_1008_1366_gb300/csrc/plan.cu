@@ -14,6 +14,8 @@ KindShape kind_shape(int kind) {
     case K_COMPLEX_ADJ:   return {2, 3, 2, 3, 2};
     case K_HERMITIAN_ADJ: return {3, 2, 2, 3, 2};
     case K_HERMITIAN_PAIR: return {3, 2, 2, 3, 2};
+    case K_COMPLEX_DOT2:  return {2, 4, 1, 4, 1};
+    case K_HERMITIAN_DOT2: return {3, 2, 1, 4, 1};
   }
   return {0, 0, 0, 0, 0};
 }
@@ -25,19 +27,21 @@ int64_t kind_TN(int kind, int64_t m) {
   switch (kind) {
     case K_HERMITIAN:
     case K_HERMITIAN_ADJ:
-    case K_HERMITIAN_PAIR: return 3 * m;
+    case K_HERMITIAN_PAIR:
+    case K_HERMITIAN_DOT2: return 3 * m;
     case K_TERNARY:       return 4 * m;
     default:              return 2 * m;
   }
 }
 
+// L = 2^a 3^b 5^c (any a, b, c >= 0)
 static bool factor(int64_t L, int* a, int* b, int* c) {
   if (L < 1) return false;
   *a = *b = *c = 0;
   while (L % 2 == 0) { L /= 2; ++*a; }
   while (L % 3 == 0) { L /= 3; ++*b; }
   while (L % 5 == 0) { L /= 5; ++*c; }
-  return L == 1 && *b <= 1 && *c <= 1;
+  return L == 1;
 }
 
 static int lcm(int x, int y) {
@@ -47,7 +51,7 @@ static int lcm(int x, int y) {
 }
 
 static bool e_supported(int E) {
-  static const int ok[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24};
+  static const int ok[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 15, 16, 20, 24, 30};
   for (int v : ok) if (v == E) return true;
   return false;
 }
@@ -60,11 +64,12 @@ bool make_fft_plan(int L, int emax, FftPlan* out) {
     if (pmax > emax) continue;
     FftPlan p{};
     p.L = L;
+    int lg = 0;
+    while ((1 << (lg + 1)) <= pmax) ++lg;          // log2(pmax)
+    if (b + c + a / lg + 1 > kMaxStages) continue;
     int ns = 0;
     for (int i = 0; i < c; ++i) p.r[ns++] = 5;
     for (int i = 0; i < b; ++i) p.r[ns++] = 3;
-    int lg = 0;
-    while ((1 << (lg + 1)) <= pmax) ++lg;          // log2(pmax)
     int rem = a;
     while (rem >= lg) { p.r[ns++] = (int8_t)(1 << lg); rem -= lg; }
     if (rem > 0) p.r[ns++] = (int8_t)(1 << rem);
@@ -89,10 +94,12 @@ static int largest_divisor_at_most(int n, int cap) {
   return 1;
 }
 
-// Plan of the fused engine (fft2.cuh): one E per size family (8 for 2^a,
-// 12 for 3*2^a, 10 for 5*2^a; larger E spills registers), the odd
-// radix first.  Returns a plan with E = 0 (DFT by definition, one thread per
-// element) when L is not a multiple of E.
+// Plan of the fused engine (fft2.cuh): one E per size family (FP32: 16 for
+// 2^a, 12 for 2^a 3^b, 20 for 2^a 5^c; FP64: 8, 12, 10; larger E spills
+// registers), the powers of two first and the odd radices (3 or 5, repeated
+// b or c times) last.  Returns a plan with E = 0 (DFT by definition, one
+// thread per element) when L is not a multiple of E, and when both 3 and 5
+// divide L (no E of the engine holds both radices).
 bool make_fused_plan(int L, int dsize, FftPlan* out) {
   int a, b, c;
   if (!factor(L, &a, &b, &c)) return false;
@@ -104,24 +111,27 @@ bool make_fused_plan(int L, int dsize, FftPlan* out) {
   } else {
     if (c) { E = 10; pmax = 2; } else if (b) { E = 12; pmax = 4; } else { E = 8; pmax = 8; }
   }
-  if (L % E != 0 || L < E) {
+  if (L % E != 0 || L < E || (b && c)) {
     p.E = 0;
     p.tpt = L;
     p.ns = 0;
     *out = p;
     return true;
   }
-  // powers of two first, the odd radix last: every stage then starts at a
-  // power-of-two stride Ns, and the forward transform uses the same order
-  int ns = 0;
+  // powers of two first, the odd radices last (the forward transform uses
+  // the same order); stages after the first odd one start at strides Ns
+  // that are not powers of two
   int lg = 0;
   while ((1 << (lg + 1)) <= pmax) ++lg;
+  int rs[64];
+  int ns = 0;
   int rem = a;
-  while (rem >= lg) { p.r[ns++] = (int8_t)(1 << lg); rem -= lg; }
-  if (rem > 0) p.r[ns++] = (int8_t)(1 << rem);
-  if (b) p.r[ns++] = 3;
-  if (c) p.r[ns++] = 5;
+  while (rem >= lg) { rs[ns++] = 1 << lg; rem -= lg; }
+  if (rem > 0) rs[ns++] = 1 << rem;
+  for (int i = 0; i < b; ++i) rs[ns++] = 3;
+  for (int i = 0; i < c; ++i) rs[ns++] = 5;
   if (ns > kMaxStages) return false;
+  for (int s = 0; s < ns; ++s) p.r[s] = (int8_t)rs[s];
   if (ns == 1) {          // one stage: the DFT by definition is as cheap
     p.E = 0;
     p.tpt = L;

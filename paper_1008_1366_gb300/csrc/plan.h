@@ -20,7 +20,10 @@ enum Kind : int32_t {
   K_HERMITIAN_ADJ = 4, // gradient of K_HERMITIAN
   K_HERMITIAN_PAIR = 5,// two Hermitian convolutions (W, g) and (W, f) sharing W (rows of
                        // the multi-D Hermitian gradient)
+  K_COMPLEX_DOT2 = 6,  // f1 * g1 + f2 * g2, complex (Sec. 3, 2D pseudospectral application)
+  K_HERMITIAN_DOT2 = 7,// f1 * g1 + f2 * g2, centered Hermitian (same passage)
 };
+constexpr int kNumKinds = 8;
 
 // Shape of one kind: q residues, NARR shared-memory arrays per residue
 // (backward transforms), NFWD forward transforms, NIN inputs, NOUT outputs.

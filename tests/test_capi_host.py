@@ -61,3 +61,23 @@ def test_null_and_bad_dtype_rejected_without_gpu(lib):
     assert lib.dc_conv_complex_1d(ctypes.c_void_p(4104), p, ctypes.c_void_p(8192), 16, 1, p, 1 << 20, None) == 3
     # partial overlap of output and input
     assert lib.dc_conv_complex_1d(p, ctypes.c_void_p(1 << 20), ctypes.c_void_p(4096 + 64), 16, 0, p, 1 << 20, None) == 1
+
+
+def _ws(lib, kind, dims, dtype=0):
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    out = ctypes.c_size_t(0)
+    return lib.dc_workspace_size(kind, len(dims), d, dtype, ctypes.byref(out))
+
+
+def test_sizes_with_repeated_odd_factors_are_planned(lib):
+    # m = 2^a 3^b 5^c: odd Hermitian lengths (Sec. 2.3) and repeated odd
+    # factors are planned; other primes are refused with DC_ERR_SIZE
+    for m in [9, 15, 25, 27, 45, 75, 81, 125, 135, 225, 243, 405, 18, 90, 720, 2880, 3600, 9216, 12800]:
+        for dtype in (0, 1):
+            assert _ws(lib, 1, [m], dtype) == 0, (m, dtype)
+            assert _ws(lib, 0, [m], dtype) == 0, (m, dtype)
+    for m in [7, 11, 13, 49, 77, 1001]:
+        assert _ws(lib, 1, [m]) == 2, m
+    for dims in [[9, 15], [15, 45], [45, 12], [3, 9, 5], [27, 75]]:
+        assert _ws(lib, 1, dims) == 0, dims
+        assert _ws(lib, 0, dims) == 0, dims
