@@ -677,36 +677,45 @@ dc_status dc_conv_complex_1d_batched_host(dc_batched_plan* p, const void* hf, co
   for (auto& q : c.st) DC_CUDA_TRY(cudaStreamWaitEvent(q, start, 0));
   auto bytes_of = [&](int k) { return (size_t)(p->off_host[c.first[k + 1]] - p->off_host[c.first[k]]) * a8; };
   auto at = [&](const void* base, int k) { return (const char*)base + (size_t)p->off_host[c.first[k]] * a8; };
-  // f and g come in on one stream (a second one measured no faster: the
-  // host link is the limit), h goes out on another
-  for (int k = 0; k < nc; ++k) {
-    DC_CUDA_TRY(cudaMemcpyAsync((void*)at(df, k), at(hf, k), bytes_of(k), cudaMemcpyHostToDevice, c.st[0]));
-    DC_CUDA_TRY(cudaEventRecord(evf[k], c.st[0]));
-    DC_CUDA_TRY(cudaMemcpyAsync((void*)at(dg, k), at(hg, k), bytes_of(k), cudaMemcpyHostToDevice, c.st[0]));
-    DC_CUDA_TRY(cudaEventRecord(evg[k], c.st[0]));
+  // Everything from here on is enqueued on the forked streams; whatever
+  // fails, `stream` is joined to them before returning, so that copies
+  // already queued on the caller's host buffers finish before any later
+  // work on `stream` (or a synchronize of it) lets the caller reuse them.
+  auto enqueue = [&]() -> dc_status {
+    // f and g come in on one stream (a second one measured no faster: the
+    // host link is the limit), h goes out on another
+    for (int k = 0; k < nc; ++k) {
+      DC_CUDA_TRY(cudaMemcpyAsync((void*)at(df, k), at(hf, k), bytes_of(k), cudaMemcpyHostToDevice, c.st[0]));
+      DC_CUDA_TRY(cudaEventRecord(evf[k], c.st[0]));
+      DC_CUDA_TRY(cudaMemcpyAsync((void*)at(dg, k), at(hg, k), bytes_of(k), cudaMemcpyHostToDevice, c.st[0]));
+      DC_CUDA_TRY(cudaEventRecord(evg[k], c.st[0]));
+    }
+    for (int k = 0; k < nc; ++k) {
+      DC_CUDA_TRY(cudaStreamWaitEvent(c.st[1], evf[k], 0));
+      DC_CUDA_TRY(cudaStreamWaitEvent(c.st[1], evg[k], 0));
+      const dc_status e = dc_conv_complex_1d_batched(c.plans[k], at(df, k), at(dg, k), (void*)at(dh, k), work,
+                                                     work_bytes, c.st[1]);
+      if (e != DC_OK) return e;
+      DC_CUDA_TRY(cudaEventRecord(evh[k], c.st[1]));
+    }
+    for (int k = 0; k < nc; ++k) {
+      DC_CUDA_TRY(cudaStreamWaitEvent(c.st[2], evh[k], 0));
+      DC_CUDA_TRY(cudaMemcpyAsync((void*)at(hh, k), at(dh, k), bytes_of(k), cudaMemcpyDeviceToHost, c.st[2]));
+    }
+    return DC_OK;
+  };
+  st = enqueue();
+  // `stream` continues after all four, on success and on failure alike
+  const cudaEvent_t joins[4] = {j0, j1, j2, j3};
+  for (int q = 0; q < 4; ++q) {
+    const cudaError_t e1 = cudaEventRecord(joins[q], c.st[q]);
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(s, joins[q], 0) : e1;
+    if (e2 != cudaSuccess && st == DC_OK) {
+      dc_set_last_cuda_error(e2);
+      st = DC_ERR_CUDA;
+    }
   }
-  for (int k = 0; k < nc; ++k) {
-    DC_CUDA_TRY(cudaStreamWaitEvent(c.st[1], evf[k], 0));
-    DC_CUDA_TRY(cudaStreamWaitEvent(c.st[1], evg[k], 0));
-    st = dc_conv_complex_1d_batched(c.plans[k], at(df, k), at(dg, k), (void*)at(dh, k), work, work_bytes,
-                                    c.st[1]);
-    if (st != DC_OK) return st;
-    DC_CUDA_TRY(cudaEventRecord(evh[k], c.st[1]));
-  }
-  for (int k = 0; k < nc; ++k) {
-    DC_CUDA_TRY(cudaStreamWaitEvent(c.st[2], evh[k], 0));
-    DC_CUDA_TRY(cudaMemcpyAsync((void*)at(hh, k), at(dh, k), bytes_of(k), cudaMemcpyDeviceToHost, c.st[2]));
-  }
-  // `stream` continues after all four
-  DC_CUDA_TRY(cudaEventRecord(j0, c.st[0]));
-  DC_CUDA_TRY(cudaEventRecord(j1, c.st[1]));
-  DC_CUDA_TRY(cudaEventRecord(j2, c.st[2]));
-  DC_CUDA_TRY(cudaEventRecord(j3, c.st[3]));
-  DC_CUDA_TRY(cudaStreamWaitEvent(s, j0, 0));
-  DC_CUDA_TRY(cudaStreamWaitEvent(s, j1, 0));
-  DC_CUDA_TRY(cudaStreamWaitEvent(s, j2, 0));
-  DC_CUDA_TRY(cudaStreamWaitEvent(s, j3, 0));
-  return DC_OK;
+  return st;
 }
 
 dc_status dc_batched_plan_destroy(dc_batched_plan* p) {
