@@ -393,6 +393,69 @@ def run_suite(args, only=None, peak=None):
         N = 4 * 2048 * 2048
         emit("2D complex 2048x2048 c64", ms, ts, 3 * f.size * 8, rel(h, ref), 5e-7 * np.log2(N),
              _pointwise_ratio(h, ref, N, U[torch.complex64], nrm(f, g)))
+    if want("2D ternary"):
+        # next row f1: the 2D ternary Hermitian convolution at the shape of the
+        # paper's Fig. 9 (mx = my = 4096), N = 4m per axis
+        ms2 = (4096, 4096)
+        shape = synthetic.hermitian_shape(ms2)
+        fs = [synthetic.hermitian_spectrum(shape, 1.5, 1030 + s_) for s_ in range(3)]
+        ts_ = [torch.tensor(x, dtype=torch.complex64, device=dev) for x in fs]
+        ms, ts = _time_call(lambda: dcl.conv_ternary_hermitian_nd(*ts_), max(5, reps // 4))
+        h = dcl.conv_ternary_hermitian_nd(*ts_).cpu().numpy()
+        ref = oracle.padded_ternary_hermitian(*fs)
+        ext = [oracle.hermitian_extend(oracle.project_hermitian(a)) for a in fs]
+        n2 = [np.linalg.norm(a) for a in ext]
+        n1 = [np.abs(a).sum() for a in ext]
+        S3 = n2[0] * n2[1] * n1[2] + n2[0] * n2[2] * n1[1] + n2[1] * n2[2] * n1[0]
+        N = 16 * 4096 * 4096
+        emit("2D ternary Hermitian 8191x4096 c64", ms, ts, 4 * fs[0].size * 8, rel(h, ref), 5e-7 * np.log2(N),
+             _pointwise_ratio(h, ref, N, U[torch.complex64], S3))
+        del h, ref, ext, ts_
+    if want("2D Euler"):
+        # next row f2: the 2D Euler advective term as one dot product of two
+        # pairs, beside the two separate convolutions it replaces
+        shape = synthetic.hermitian_shape((1024, 1024))
+        w = synthetic.hermitian_spectrum(shape, 1.5, 1040)
+        kx = (np.arange(shape[0]) - 1023)[:, None] * np.ones((1, shape[1]))
+        ky = np.ones((shape[0], 1)) * np.arange(shape[1])[None, :]
+        k2 = kx ** 2 + ky ** 2
+        inv = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
+        fs = [1j * kx * w, 1j * ky * w]
+        gs = [1j * ky * w * inv, -1j * kx * w * inv]
+        tf = [torch.tensor(x, dtype=torch.complex64, device=dev) for x in fs]
+        tg = [torch.tensor(x, dtype=torch.complex64, device=dev) for x in gs]
+        ms, ts = _time_call(lambda: dcl.conv_hermitian_dot2(tf[0], tg[0], tf[1], tg[1]), reps)
+        ms_sep, _ = _time_call(lambda: (dcl.conv_hermitian_nd(tf[0], tg[0]), dcl.conv_hermitian_nd(tf[1], tg[1])), reps)
+        h = dcl.conv_hermitian_dot2(tf[0], tg[0], tf[1], tg[1]).cpu().numpy()
+        ref = oracle.dot_hermitian(fs, gs)
+        N = 9 * 1024 * 1024
+        emit("2D Euler advective term (Hermitian dot product of two pairs) 2047x1024 c64", ms, ts,
+             5 * w.size * 8, rel(h, ref), 5e-7 * np.log2(N),
+             _pointwise_ratio(h, ref, N, U[torch.complex64], hnrm(fs[0], gs[0]) + hnrm(fs[1], gs[1])),
+             {"ms_two_separate_convolutions": ms_sep})
+    if want("1D complex full"):
+        # next row f3: general padding, the full 2m - 1 outputs (p = 1, q = 2)
+        m = 8192
+        f = synthetic.uniform_complex(m, 1041)
+        g = synthetic.uniform_complex(m, 1042)
+        tf, tg = (torch.tensor(x, dtype=torch.complex64, device=dev) for x in (f, g))
+        ms, ts = _time_call(lambda: dcl.conv_complex_1d_full(tf, tg), reps)
+        h = dcl.conv_complex_1d_full(tf, tg).cpu().numpy()
+        ref = oracle.padded_complex_pq(f, g, m, 2, 2 * m - 1)
+        emit("1D complex full 2m-1 output (p/q = 1/2) m=8192 c64", ms, ts, (2 * m + 2 * m - 1) * 8, rel(h, ref),
+             5e-7 * np.log2(2 * m), _pointwise_ratio(h, ref, 2 * m, U[torch.complex64], nrm(f, g)))
+    if want("2D Hermitian odd"):
+        # next row f4: odd m = 2c + 1 on both axes (405 = 5 x 3^4)
+        ms2 = (405, 405)
+        shape = synthetic.hermitian_shape(ms2)
+        f = synthetic.hermitian_spectrum(shape, 1.5, 1043)
+        g = synthetic.hermitian_spectrum(shape, 1.5, 1044)
+        tf, tg = (torch.tensor(x, dtype=torch.complex64, device=dev) for x in (f, g))
+        ms, ts = _time_call(lambda: dcl.conv_hermitian_nd(tf, tg), reps)
+        h, ref = dcl.conv_hermitian_nd(tf, tg).cpu().numpy(), oracle.padded_hermitian(f, g)
+        N = 9 * 405 * 405
+        emit("2D Hermitian odd m 809x405 c64", ms, ts, 3 * f.size * 8, rel(h, ref), 5e-7 * np.log2(N),
+             _pointwise_ratio(h, ref, N, U[torch.complex64], hnrm(f, g)))
     if want("3D Hermitian"):
         shape = synthetic.hermitian_shape((256, 256, 256))
         N = 27 * 256 ** 3

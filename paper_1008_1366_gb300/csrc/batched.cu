@@ -210,12 +210,13 @@ dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
 }
 
 fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work,
-                   const void* e = nullptr, void* h2 = nullptr) {
+                   const void* e = nullptr, void* h2 = nullptr, const void* e2 = nullptr) {
   fx::FxArgs a{};
   a.f = f;
   a.g = g;
   a.h = h;
   a.e = e;
+  a.e2 = e2;
   a.h2 = h2;
   a.mode = p->mode;
   a.off = p->d_off;
@@ -228,7 +229,7 @@ fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void*
   a.scratch = (char*)work + p->cnt_bytes;
   a.tmp = (char*)work + fx_tmp_offset(p);
   a.l1tmp = p->d_l1tmp;
-  auto aliases = [&](const void* o) { return o && (o == f || o == g || o == e); };
+  auto aliases = [&](const void* o) { return o && (o == f || o == g || o == e || o == e2); };
   a.in_place = (aliases(h) || aliases(h2)) ? 1 : 0;
   a.wait_limit = fx::kWaitLimit;
   for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
@@ -236,9 +237,9 @@ fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void*
 }
 
 dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work, cudaStream_t s,
-                    const void* e = nullptr, void* h2 = nullptr) {
+                    const void* e = nullptr, void* h2 = nullptr, const void* e2 = nullptr) {
   DC_CUDA_TRY(cudaMemsetAsync(work, 0, p->cnt_bytes, s));
-  fx::FxArgs a = fx_args(p, f, g, h, work, e, h2);
+  fx::FxArgs a = fx_args(p, f, g, h, work, e, h2, e2);
   if (p->inst_first.empty()) return p->ops->launch(a, p->grid, p->smem, s);
   // plain mode: each instance's tasks in a launch of their own (the queue
   // counter is reset before each; the dependency counters are distinct)
@@ -820,34 +821,36 @@ dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, dc_batched_plan** out, i
 }
 
 namespace {
-std::map<std::tuple<int, int64_t, int>, dc_batched_plan*> g_tplans;   // (device, m, ds)
+std::map<std::tuple<int, int64_t, int64_t, int>, dc_batched_plan*> g_tplans;   // (device, n, m, ds)
 }  // namespace
 
 bool fx_ternary_ok(int64_t m, int ds) { return fx_uniform_ok(2 * m, ds) && fx_uniform_two_level(2 * m); }
 
-size_t fx_ternary_work(int64_t m, int ds) { return fx_uniform_work(1, 2 * m, ds, fx::MODE_TERN); }
+size_t fx_ternary_work(int64_t m, int ds, int64_t n) { return fx_uniform_work(n, 2 * m, ds, fx::MODE_TERN); }
 
-// The plan of one ternary convolution of length m on the fixed engine (a
-// one-instance plan of the M = 2m point sub-transforms whose inputs and
-// output hold m elements), cached per device and precision.
-dc_status fx_ternary_plan(int64_t m, int ds, dc_batched_plan** out) {
-  if (!fx_ternary_ok(m, ds)) return DC_ERR_SIZE;
+// The plan of n ternary convolutions of length m at stride m on the fixed
+// engine (n instances of the M = 2m point sub-transforms whose inputs and
+// outputs hold m elements: one 1D call, or the rows of a multi-D call),
+// cached per device, count and precision.
+dc_status fx_ternary_plan(int64_t m, int ds, dc_batched_plan** out, int64_t n) {
+  if (!fx_ternary_ok(m, ds) || n < 1) return DC_ERR_SIZE;
   int dev = 0;
   DC_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(g_umu);
-  auto key = std::make_tuple(dev, m, ds);
+  auto key = std::make_tuple(dev, n, m, ds);
   auto it = g_tplans.find(key);
   if (it != g_tplans.end()) { *out = it->second; return DC_OK; }
-  std::vector<int64_t> ms(1, 2 * m), off{0, m};
+  std::vector<int64_t> ms((size_t)n, 2 * m), off((size_t)n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) off[i + 1] = off[i] + m;
   dc_batched_plan* p = new dc_batched_plan();
   p->dtype = ds == 8 ? DC_C64 : DC_C128;
   p->ds = ds;
-  p->n = 1;
-  p->total = m;
+  p->n = (int32_t)n;
+  p->total = n * m;
   p->m_host = ms;
   p->off_host = off;
   p->device = dev;
-  dc_status st = create_fixed(p, ms.data(), 1, off, 0, fx::MODE_TERN);
+  dc_status st = create_fixed(p, ms.data(), (int32_t)n, off, 0, fx::MODE_TERN);
   if (st != DC_OK) { dc_batched_plan_destroy(p); return st; }
   g_tplans[key] = p;
   *out = p;
@@ -855,12 +858,19 @@ dc_status fx_ternary_plan(int64_t m, int ds, dc_batched_plan** out) {
 }
 
 dc_status fx_ternary_run(int64_t m, int ds, const void* f, const void* g, const void* e, void* h, void* work,
-                         size_t work_bytes, cudaStream_t s) {
+                         size_t work_bytes, cudaStream_t s, int64_t n) {
   dc_batched_plan* p = nullptr;
-  dc_status st = fx_ternary_plan(m, ds, &p);
+  dc_status st = fx_ternary_plan(m, ds, &p, n);
   if (st != DC_OK) return st;
   if (work_bytes < p->work) return DC_ERR_NOMEM;
   return fx_launch(p, f, g, h, work, s, e);
+}
+
+dc_status fx_hdot2_run(dc_batched_plan* p, const void* f1, const void* g1, const void* f2, const void* g2, void* h,
+                       void* work, size_t work_bytes, cudaStream_t s) {
+  if (!p || p->mode != fx::MODE_HDOT2) return DC_ERR_ARG;
+  if (work_bytes < p->work) return DC_ERR_NOMEM;
+  return fx_launch(p, f1, g1, h, work, s, f2, nullptr, g2);
 }
 
 dc_status fx_pair_run(dc_batched_plan* p, const void* w, const void* f, const void* g, void* df, void* dg,

@@ -6,8 +6,9 @@
 // x[j + q L/R], twiddles them by zeta_{Ns R}^{s q k} (k = j mod Ns, s = +1
 // backward, -1 forward), applies the radix-R DFT and scatters to
 // (j - k) R + k + q Ns.  Natural order in and out.  Plans put the powers of
-// two first and the odd radix last, so every stage starts at a power-of-two
-// stride Ns (k is a mask, not a division); both directions use that order.
+// two first and the odd radices last, so every stage up to the first odd one
+// starts at a power-of-two stride Ns (k is a mask there, a division after
+// it); both directions use that order.
 // The pointwise product is fused into the first forward stage (conv1d.cuh).
 //
 // Roots of unity come from two short tables in shared memory,

@@ -26,8 +26,14 @@ enum : int32_t { T_L1 = 0, T_A = 1, T_B = 2, T_C = 3 };
 //   MODE_PAIR     rows of a centered Hermitian gradient: inputs (W, f, g) in
 //                 (f, g, e), outputs conv(W, g) in h and conv(W, f) in h2,
 //                 tables of zeta_{3m}, one-level sizes only
-enum : int32_t { MODE_COMPLEX = 0, MODE_HERM = 1, MODE_TERN = 2, MODE_PAIR = 3 };
-__host__ __device__ constexpr bool mode_tables_3m(int mode) { return mode == MODE_HERM || mode == MODE_PAIR; }
+//   MODE_HDOT2    dot product of two centered Hermitian pairs (arrays of
+//                 vectors, Sec. 3): inputs (f1, g1, f2, g2) in (f, g, e, e2),
+//                 output f1 * g1 + f2 * g2 in h, tables of zeta_{3m},
+//                 one-level sizes only
+enum : int32_t { MODE_COMPLEX = 0, MODE_HERM = 1, MODE_TERN = 2, MODE_PAIR = 3, MODE_HDOT2 = 4 };
+__host__ __device__ constexpr bool mode_tables_3m(int mode) {
+  return mode == MODE_HERM || mode == MODE_PAIR || mode == MODE_HDOT2;
+}
 
 // One queue entry.  kc = type << 8 | size code.  T_L1: a = first slot of
 // the order array, b = instance count.  T_A/T_B/T_C: a = level-2 instance,
@@ -51,7 +57,8 @@ struct FxArgs {
   const void* f;
   const void* g;
   void* h;
-  const void* e;           // third input (ternary: e; gradient pair: g)
+  const void* e;           // third input (ternary: e; gradient pair: g; dot product: f2)
+  const void* e2;          // fourth input (dot product: g2)
   void* h2;                // second output (gradient pair)
   const int64_t* off;      // per-instance element offsets
   const int32_t* order;    // instance ids of the level-1 tasks

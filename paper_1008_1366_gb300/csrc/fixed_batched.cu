@@ -319,6 +319,60 @@ __device__ __noinline__ void l1_pair_residue(const FxArgs* a, int ri, int first,
       sync);
 }
 
+// product of the dot product of two centered Hermitian pairs: the first
+// array holds u^{f1} + i u^{g1}, the second u^{f2} + i u^{g2} (all four
+// real), and the sum of the two real products is real
+struct HDot2Prod {
+  __device__ __forceinline__ C operator()(C a, C b) const {
+    C p;
+    p.x = a.x * a.y + b.x * b.y;
+    p.y = 0;
+    return p;
+  }
+};
+
+// level 1, dot product of two centered Hermitian pairs (Sec. 3, arrays of
+// vectors; Sec. 2.3 per pair): residue ri (r = ri - 1) of `count`
+// instances.  The group's two arrays take the packed inputs
+// w^{f1} + i w^{g1} and w^{f2} + i w^{g2}; both backward transforms, the
+// summed real product, one forward transform; the output adds
+// zeta_{3m}^{-rk} S_r(k) / 3m.  The residue sum is kept in h, or, for
+// in-place calls (h one of the inputs), in a workspace slot, and h is
+// written at the last residue.
+template <int M>
+__device__ __noinline__ void l1_hdot2_residue(const FxArgs* a, int ri, int first, int count, C* sm, Roots<C> rt) {
+  using S = Shape<M>;
+  constexpr int E = S::E, T = S::T, PL = padded(M), GS = group_stride(M, T), TN = 3 * M;
+  const int gi = threadIdx.x / T, i = threadIdx.x % T;
+  const bool act = gi < count;
+  const int64_t off = act ? a->off[a->order[first + gi]] : 0;
+  const C* f1 = (const C*)a->f + off;
+  const C* g1 = (const C*)a->g + off;
+  const C* f2 = (const C*)a->e + off;
+  const C* g2 = (const C*)a->e2 + off;
+  C* h = (C*)a->h + off;
+  C* p = a->in_place ? (C*)a->tmp + (act ? a->l1tmp[a->order[first + gi]] : 0) : h;
+  C* A = sm + gi * GS;
+  const Real sc = (Real)1 / (Real)(3 * M);
+  const GroupSync<T> sync{1 + gi};
+  const HermTerms ht(ri - 1);
+  conv_residue<M, E, TN>(
+      i, true, A, A + PL, rt,
+      [&](int x, int arr, int) {
+        C v = arr ? ht.packed<M>(f2, g2, x, rt) : ht.packed<M>(f1, g1, x, rt);
+        if (!act) v.x = v.y = 0;
+        return v;
+      },
+      [&](int x, int, C v) {
+        if (!act) return;
+        v = cscale(ht.out(v, x, rt), sc);
+        if (ri == 0) p[x] = v;
+        else if (ri == 1) p[x] = cadd(p[x], v);
+        else h[x] = cadd(p[x], v);
+      },
+      sync, HDot2Prod{});
+}
+
 // pass A: column tile `tile` of level-2 instance l.  Each pass is its own
 // function so that registers are allocated per pass.
 template <int M>
@@ -690,13 +744,20 @@ __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C
         l1_pair_residue<M>(a, ri, x, y, sm, rt);
         __syncthreads();
       }
+    } else if constexpr (MODE == MODE_HDOT2) {
+#pragma unroll 1
+      for (int ri = 0; ri < 3; ++ri) {
+        l1_hdot2_residue<M>(a, ri, x, y, sm, rt);
+        __syncthreads();
+      }
     } else {
       // ternary plans hold two-level sizes only (the planner refuses others)
       if (threadIdx.x == 0) record_error(a->hdr, DC_ERR_DEVICE, M);
     }
   } else {
-    if constexpr (MODE == MODE_PAIR) {
-      // gradient-pair plans hold one-level sizes only (the planner refuses others)
+    if constexpr (MODE == MODE_PAIR || MODE == MODE_HDOT2) {
+      // gradient-pair and dot-product plans hold one-level sizes only (the
+      // planner refuses others)
       if (threadIdx.x == 0) record_error(a->hdr, DC_ERR_DEVICE, M);
     } else if constexpr (MODE == MODE_HERM) {
       if (type == T_A) run_A_herm<M>(a, x, y, sm, rt);
@@ -881,7 +942,8 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   for (int32_t i = 0; i < n; ++i) {
     const int c = size_code(m[i]);
     if (c < 0) return false;
-    if ((mode == MODE_TERN && tb.lvl[c] == 1) || (mode == MODE_PAIR && tb.lvl[c] == 2)) return false;
+    if ((mode == MODE_TERN && tb.lvl[c] == 1) || ((mode == MODE_PAIR || mode == MODE_HDOT2) && tb.lvl[c] == 2))
+      return false;
     used[c] = true;
     if (tb.lvl[c] == 1) {
       l1_by_code[c].push_back(i);
@@ -1014,7 +1076,8 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
 
 dc_status prepare_kernel(int smem, int* blocks_per_sm) {
   int bmin = 1 << 20;
-  for (auto k : {fx_kernel<MODE_COMPLEX>, fx_kernel<MODE_HERM>, fx_kernel<MODE_TERN>, fx_kernel<MODE_PAIR>}) {
+  for (auto k : {fx_kernel<MODE_COMPLEX>, fx_kernel<MODE_HERM>, fx_kernel<MODE_TERN>, fx_kernel<MODE_PAIR>,
+                 fx_kernel<MODE_HDOT2>}) {
     DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int b = 0;
     DC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kThreads, smem));
@@ -1031,6 +1094,7 @@ dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s) {
     case MODE_HERM: fx_kernel<MODE_HERM><<<grid, kThreads, smem, s>>>(a); break;
     case MODE_TERN: fx_kernel<MODE_TERN><<<grid, kThreads, smem, s>>>(a); break;
     case MODE_PAIR: fx_kernel<MODE_PAIR><<<grid, kThreads, smem, s>>>(a); break;
+    case MODE_HDOT2: fx_kernel<MODE_HDOT2><<<grid, kThreads, smem, s>>>(a); break;
     default: return DC_ERR_ARG;
   }
   DC_CUDA_TRY(cudaGetLastError());

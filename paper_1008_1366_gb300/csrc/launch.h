@@ -36,13 +36,18 @@ dc_status fx_uniform_plan(int64_t n, int64_t m, int ds, struct dc_batched_plan**
 // df = conv(w, g), dg = conv(w, f); outputs may be inputs
 dc_status fx_pair_run(struct dc_batched_plan* p, const void* w, const void* f, const void* g, void* df, void* dg,
                       void* work, size_t work_bytes, cudaStream_t s);
-// one centered Hermitian ternary convolution of length m on the fixed engine
-// (2m a two-level size of the set)
+// the rows of a dot product of two centered Hermitian pairs on a MODE_HDOT2
+// plan: h = f1 * g1 + f2 * g2; h may be an input
+dc_status fx_hdot2_run(struct dc_batched_plan* p, const void* f1, const void* g1, const void* f2, const void* g2,
+                       void* h, void* work, size_t work_bytes, cudaStream_t s);
+// n centered Hermitian ternary convolutions of length m at stride m on the
+// fixed engine (2m a two-level size of the set): one 1D call, or the rows of
+// a multi-D call; outputs may be inputs
 bool fx_ternary_ok(int64_t m, int ds);
-size_t fx_ternary_work(int64_t m, int ds);
-dc_status fx_ternary_plan(int64_t m, int ds, struct dc_batched_plan** out);
+size_t fx_ternary_work(int64_t m, int ds, int64_t n = 1);
+dc_status fx_ternary_plan(int64_t m, int ds, struct dc_batched_plan** out, int64_t n = 1);
 dc_status fx_ternary_run(int64_t m, int ds, const void* f, const void* g, const void* e, void* h, void* work,
-                         size_t work_bytes, cudaStream_t s);
+                         size_t work_bytes, cudaStream_t s, int64_t n = 1);
 dc_status conv1d_blocks_per_sm(int kind, int dsize, int smem, int* out);
 
 // general implicit padding (pq.cu): checks and plans a call (the m-point

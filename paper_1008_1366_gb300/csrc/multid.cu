@@ -36,6 +36,7 @@ int row_mode(int row_kind) {
     case K_COMPLEX: return fx::MODE_COMPLEX;
     case K_HERMITIAN: return fx::MODE_HERM;
     case K_HERMITIAN_PAIR: return fx::MODE_PAIR;
+    case K_HERMITIAN_DOT2: return fx::MODE_HDOT2;
   }
   return -1;
 }
@@ -168,8 +169,21 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   // channel).
   md->rows_mode = row_mode(md->row_kind);
   md->rows_fx = fx_uniform_ok(mlast, ds) && md->rows_mode >= 0 &&
-                (md->rows_mode != fx::MODE_PAIR || !fx_uniform_two_level(mlast));
-  if (md->rows_fx) {
+                ((md->rows_mode != fx::MODE_PAIR && md->rows_mode != fx::MODE_HDOT2) || !fx_uniform_two_level(mlast));
+  // ternary rows whose 2m-point sub-transforms are a two-level size of the
+  // set run on the fixed engine's ternary passes
+  if (md->tern && fx_ternary_ok(mlast, ds)) {
+    md->rows_fx = true;
+    md->rows_mode = fx::MODE_TERN;
+    rows_bytes = std::max(fx_ternary_work(mlast, ds, md->rows_n[0]), fx_ternary_work(mlast, ds, md->rows_n[1]));
+    if (with_tables) {
+      for (int k = 0; k < 2; ++k) {
+        dc_batched_plan* p = nullptr;
+        dc_status st = fx_ternary_plan(mlast, ds, &p, md->rows_n[k]);
+        if (st != DC_OK) return st;
+      }
+    }
+  } else if (md->rows_fx) {
     rows_bytes = std::max(fx_uniform_work(md->rows_n[0], mlast, ds, md->rows_mode),
                           fx_uniform_work(md->rows_n[1], mlast, ds, md->rows_mode));
     if (with_tables) {
@@ -190,12 +204,14 @@ dc_status run_rows(const Md& md, const void* const* in, void* const* out, int64_
   if (md.rows_fx) {
     // the rows' own status header sits at the start of their region
     const int64_t m = md.m[md.ndim - 1];
+    char* rw = work + md.off_rows;
+    const size_t rb = md.total - md.off_rows;
+    if (md.rows_mode == fx::MODE_TERN) return fx_ternary_run(m, md.ds, in[0], in[1], in[2], out[0], rw, rb, s, nrows);
     dc_batched_plan* p = nullptr;
     dc_status st = fx_uniform_plan(nrows, m, md.ds, &p, md.rows_mode);
     if (st != DC_OK) return st;
-    char* rw = work + md.off_rows;
-    const size_t rb = md.total - md.off_rows;
     if (md.rows_mode == fx::MODE_PAIR) return fx_pair_run(p, in[0], in[1], in[2], out[0], out[1], rw, rb, s);
+    if (md.rows_mode == fx::MODE_HDOT2) return fx_hdot2_run(p, in[0], in[1], in[2], in[3], out[0], rw, rb, s);
     return dc_conv_complex_1d_batched(p, in[0], in[1], out[0], rw, rb, s);
   }
   ConvArgs a{};
