@@ -612,8 +612,16 @@ def main():
     # where the kernel's blocks spent their cycles (last launch of the loop)
     trace = dcl.read_trace(work)
     busy = sum(trace["cycles"].values())
+    # block-cycles of the launch: blocks x duration x SM clock (sampled)
+    clk_mhz = clk.summary().get("sm_mhz") or 2070.0
+    # (the FP32 fixed-shape kernel runs two blocks per SM)
+    launch_cycles = 2 * torch.cuda.get_device_properties(dev).multi_processor_count * \
+        statistics.mean(per) * 1e-3 * clk_mhz * 1e6
     trace = {"tasks": trace["tasks"], "cycle_share": {k: round(v / max(1, busy), 4) for k, v in trace["cycles"].items()},
-             "tasks_that_waited": trace["waited"], "wait_cycles_over_task_cycles": round(trace["wait_cycles"] / max(1, busy), 5)}
+             "tasks_that_waited": trace["waited"], "wait_cycles_over_task_cycles": round(trace["wait_cycles"] / max(1, busy), 5),
+             "block_time_share": {"in_tasks": round(busy / launch_cycles, 4),
+                                  "handover": round(trace["handover_cycles"] / launch_cycles, 4),
+                                  "root_tables": round(trace["table_cycles"] / launch_cycles, 4)}}
     convs_total = len(sizes) * args.steps
     value = convs_total / (t_ms / 1e3)
     ms_step = t_ms / args.steps
@@ -737,7 +745,8 @@ def main():
                        "parallelism": (f"{world} ranks, one batch split by longest-processing-time partition "
                                        f"(cost m log2 m), no collective on the data path"),
                        "partition_max_over_mean_load": max(loads) / (sum(loads) / world),
-                       "schedule": plan.schedule()},
+                       "schedule": {"batch_target_tiles": plan.schedule()[0], "l1_placement": plan.schedule()[1],
+                                    "task_units": plan.task_units()}},
             "roofline": roof,
             "step_ms_stats": {"mean": T_mean, "sigma_L": sig_l, "sigma_H": sig_h, "median": statistics.median(per)},
             "cpu_baseline": cpu,

@@ -114,8 +114,10 @@ dc_status dc_read_status(const void* work, void* stream, int32_t* status, int32_
  * (workspace header), after synchronizing `stream`; no counterpart in the
  * paper.  out[0] = tasks that found their dependency unmet, out[1] = SM
  * cycles they waited, out[2..5] = SM cycles spent in level-1 tasks and in
- * the tasks of passes A, B, C, out[6..9] = the number of such tasks.  Other
- * kernels leave them zero. */
+ * the tasks of passes A, B, C, out[6..9] = the number of such tasks,
+ * out[10] = SM cycles between the end of a task and the start of the next
+ * (queue, dependency check), out[11] = SM cycles spent loading root tables
+ * (12 entries).  Other kernels leave them zero. */
 dc_status dc_read_trace(const void* work, void* stream, uint64_t* out);
 
 /* ---------------------------------------------------------------------------
@@ -322,6 +324,15 @@ dc_status dc_batched_plan_schedule(const dc_batched_plan* plan, int32_t* batch_t
  * The workspace size may change: query it again.  Not while a launch of the
  * plan is in flight.  DC_ERR_ARG for other plans or values. */
 dc_status dc_batched_plan_set_schedule(dc_batched_plan* plan, int32_t batch_target, int32_t l1_mode);
+/* Column tiles (passes A, C) or row groups (pass B) each task of such a plan
+ * runs, 1 to 4 (no counterpart in the paper: fewer, longer tasks spend less
+ * of the launch handing over between tasks, more keep the blocks balanced).
+ * DC_PLAN_AUTOTUNE picks it with the queue order; _set_ rebuilds the queue
+ * with the given value (same result, other timing; query the workspace size
+ * again; not while a launch of the plan is in flight).  DC_ERR_ARG for other
+ * plans or values. */
+dc_status dc_batched_plan_task_units(const dc_batched_plan* plan, int32_t* units);
+dc_status dc_batched_plan_set_task_units(dc_batched_plan* plan, int32_t units);
 dc_status dc_conv_complex_1d_batched(const dc_batched_plan* plan, const void* f, const void* g,
                                      void* h, void* work, size_t work_bytes, void* stream);
 /* Failure-path self-test, no counterpart in the paper: launches the

@@ -108,11 +108,12 @@ def read_status(work):
 def read_trace(work):
     """Trace counters of the last fixed-engine launch on `work`
     (dc_read_trace): waits, and SM cycles / task counts per task type."""
-    out = (ctypes.c_uint64 * 10)()
+    out = (ctypes.c_uint64 * 12)()
     check(_native.lib().dc_read_trace(_vp(work), _stream(work), out), "dc_read_trace")
     names = ("L1", "A", "B", "C")
     return {"waited": out[0], "wait_cycles": out[1],
-            "cycles": dict(zip(names, out[2:6])), "tasks": dict(zip(names, out[6:10]))}
+            "cycles": dict(zip(names, out[2:6])), "tasks": dict(zip(names, out[6:10])),
+            "handover_cycles": out[10], "table_cycles": out[11]}
 
 
 def _run_1d(name, kind, ins, nout, out):
@@ -333,6 +334,24 @@ class BatchedPlan:
         """Rebuilds the task queue in the given order (dc_batched_plan_set_schedule)."""
         check(_native.lib().dc_batched_plan_set_schedule(self.handle, int(batch_target), int(l1_mode)),
               "dc_batched_plan_set_schedule")
+        ws = ctypes.c_size_t(0)
+        check(_native.lib().dc_batched_plan_workspace_size(self.handle, ctypes.byref(ws)), "workspace")
+        self.workspace_bytes = int(ws.value)
+        self._work = None
+
+    def task_units(self):
+        """Tiles or row groups per pass task (dc_batched_plan_task_units), or
+        None for plans on the runtime-shaped engine."""
+        u = ctypes.c_int32(0)
+        if _native.lib().dc_batched_plan_task_units(self.handle, ctypes.byref(u)) != 0:
+            return None
+        return u.value
+
+    def set_task_units(self, units):
+        """Rebuilds the task queue with this many tiles or row groups per pass
+        task (dc_batched_plan_set_task_units)."""
+        check(_native.lib().dc_batched_plan_set_task_units(self.handle, int(units)),
+              "dc_batched_plan_set_task_units")
         ws = ctypes.c_size_t(0)
         check(_native.lib().dc_batched_plan_workspace_size(self.handle, ctypes.byref(ws)), "workspace")
         self.workspace_bytes = int(ws.value)

@@ -300,7 +300,7 @@ bool fx_build_plain(dc_batched_plan* p, const int64_t* m, int32_t n, const std::
     p->inst_first.push_back((int32_t)all.tasks.size());
     p->inst_count.push_back((int32_t)one.tasks.size());
     for (fx::Task t : one.tasks) {
-      if ((t.kc >> 8) == fx::T_L1) t.a += ob;
+      if (((t.kc >> 8) & 255) == fx::T_L1) t.a += ob;
       else t.a += lb;
       if (t.widx >= 0) t.widx += cb;
       if (t.sidx >= 0) t.sidx += cb;
@@ -350,18 +350,21 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
   p->fx_sched = dflt;
   if ((flags & DC_PLAN_AUTOTUNE) && !plain) {
     // the queue order: pipeline distance between the level-2 passes (waits
-    // against scratch footprint in L2) and the placement of level-1 work
+    // against scratch footprint in L2), the placement of level-1 work, and
+    // the tiles or row groups per pass task (hand-over against balance)
     cudaStream_t s;
     DC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     fx::Schedule best = dflt;
     float tbest = fx_time(p, s);
     for (int cand : {p->grid / 4, p->grid / 2, p->grid}) {
       for (int mode = 0; mode < fx::kL1Modes; ++mode) {
-        const fx::Schedule sc{cand, mode};
-        if (cand < 1 || (cand == dflt.batch_target && mode == dflt.l1_mode)) continue;
-        if (!p->ops->build_plan(m, n, off.data(), sc, p->mode, &p->hp) || fx_upload(p, off) != DC_OK) continue;
-        const float t = fx_time(p, s);
-        if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; best = sc; }
+        for (int units : {1, 2, 4}) {
+          const fx::Schedule sc{cand, mode, units};
+          if (cand < 1 || (cand == dflt.batch_target && mode == dflt.l1_mode && units == dflt.units)) continue;
+          if (!p->ops->build_plan(m, n, off.data(), sc, p->mode, &p->hp) || fx_upload(p, off) != DC_OK) continue;
+          const float t = fx_time(p, s);
+          if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; best = sc; }
+        }
       }
     }
     cudaStreamDestroy(s);
@@ -569,7 +572,25 @@ dc_status dc_batched_plan_set_schedule(dc_batched_plan* p, int32_t batch_target,
     return DC_ERR_ARG;
   std::vector<int64_t> ms(p->n);
   for (int32_t i = 0; i < p->n; ++i) ms[i] = p->off_host[i + 1] - p->off_host[i];
-  const fx::Schedule sc{batch_target, l1_mode};
+  const fx::Schedule sc{batch_target, l1_mode, p->fx_sched.units};
+  if (!p->ops->build_plan(ms.data(), p->n, p->off_host.data(), sc, p->mode, &p->hp)) return DC_ERR_SIZE;
+  dc_status st = fx_upload(p, p->off_host);
+  if (st != DC_OK) return st;
+  p->fx_sched = sc;
+  return DC_OK;
+}
+
+dc_status dc_batched_plan_task_units(const dc_batched_plan* p, int32_t* units) {
+  if (!p || !p->fx || !p->inst_first.empty() || !units) return DC_ERR_ARG;
+  *units = p->fx_sched.units;
+  return DC_OK;
+}
+
+dc_status dc_batched_plan_set_task_units(dc_batched_plan* p, int32_t units) {
+  if (!p || !p->fx || !p->inst_first.empty() || units < 1 || units > fx::kMaxUnits) return DC_ERR_ARG;
+  std::vector<int64_t> ms(p->n);
+  for (int32_t i = 0; i < p->n; ++i) ms[i] = p->off_host[i + 1] - p->off_host[i];
+  const fx::Schedule sc{p->fx_sched.batch_target, p->fx_sched.l1_mode, units};
   if (!p->ops->build_plan(ms.data(), p->n, p->off_host.data(), sc, p->mode, &p->hp)) return DC_ERR_SIZE;
   dc_status st = fx_upload(p, p->off_host);
   if (st != DC_OK) return st;

@@ -271,6 +271,8 @@ dc_status dc_read_trace(const void* work, void* stream, uint64_t* out) {
     out[2 + k] = h.type_cycles[k];
     out[6 + k] = h.type_count[k];
   }
+  out[10] = h.handover_cycles;
+  out[11] = h.table_cycles;
   return DC_OK;
 }
 

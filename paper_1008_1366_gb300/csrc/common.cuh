@@ -44,7 +44,9 @@ struct WorkHeader {
   unsigned long long wait_cycles;   // and the SM cycles they spent waiting
   unsigned long long type_cycles[4];   // SM cycles spent in tasks of each type
   uint32_t type_count[4];              // and the number of such tasks
-  uint32_t pad[46];
+  unsigned long long handover_cycles;  // cycles from a task's end to the next one's start (queue, dependency)
+  unsigned long long table_cycles;     // cycles spent loading root tables into shared memory
+  uint32_t pad[42];
 };
 static_assert(sizeof(WorkHeader) == 256, "workspace header is 256 bytes");
 

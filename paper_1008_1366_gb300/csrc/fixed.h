@@ -35,11 +35,13 @@ __host__ __device__ constexpr bool mode_tables_3m(int mode) {
   return mode == MODE_HERM || mode == MODE_PAIR || mode == MODE_HDOT2;
 }
 
-// One queue entry.  kc = type << 8 | size code.  T_L1: a = first slot of
-// the order array, b = instance count.  T_A/T_B/T_C: a = level-2 instance,
-// b = column tile (A, C) or row group (B).  Before it starts the task waits
-// until cnt[widx] >= wneed (widx < 0: no wait); when done it adds one to
-// cnt[sidx] (sidx < 0: none).  Every wait names a counter that only tasks
+// One queue entry.  kc = units << 16 | type << 8 | size code.  T_L1: a =
+// first slot of the order array, b = instance count.  T_A/T_B/T_C: a =
+// level-2 instance, b = the first of `units` consecutive column tiles (A, C)
+// or row groups (B) the task runs.  Before it starts the task waits until
+// cnt[widx] >= wneed (widx < 0: no wait); when done it adds its units (one
+// for T_L1) to cnt[sidx] (sidx < 0: none), so thresholds count tiles and row
+// groups whatever the grouping.  Every wait names a counter that only tasks
 // earlier in the queue advance.
 struct Task {
   int32_t kc, a, b, widx;
@@ -93,11 +95,14 @@ struct HostPlan {
 // instances (the pipeline distance between passes).  l1_mode: where the
 // level-1 tasks go (largest first in every mode): 0 after the level-2
 // pipeline, 1 the larger half spread over the pipeline and the rest after
-// it, 2 before it.
+// it, 2 before it.  units: column tiles or row groups per pass task (1, 2
+// or 4): fewer, longer tasks spend less of the launch handing over.
 struct Schedule {
   int batch_target;
   int l1_mode;
+  int units = 1;
 };
+constexpr int kMaxUnits = 4;
 constexpr int kL1Modes = 3;
 constexpr long long kWaitLimit = 1ll << 32;   // about two seconds at 2 GHz
 

@@ -726,7 +726,7 @@ __device__ __noinline__ void run_C_herm(const FxArgs* a, int l, int tile, C* sm,
 // passes.
 
 template <int M, int MODE>
-__device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C* sm, Roots<C> rt) {
+__device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, int units, C* sm, Roots<C> rt) {
   if constexpr (Shape<M>::l1) {
     if constexpr (MODE == MODE_HERM) {
 #pragma unroll 1
@@ -759,18 +759,26 @@ __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, C
       // gradient-pair and dot-product plans hold one-level sizes only (the
       // planner refuses others)
       if (threadIdx.x == 0) record_error(a->hdr, DC_ERR_DEVICE, M);
-    } else if constexpr (MODE == MODE_HERM) {
-      if (type == T_A) run_A_herm<M>(a, x, y, sm, rt);
-      else if (type == T_B) run_B_herm<M>(a, x, y, sm, rt);
-      else run_C_herm<M>(a, x, y, sm, rt);
-    } else if constexpr (MODE == MODE_TERN) {
-      if (type == T_A) run_A_tern<M>(a, x, y, sm, rt);
-      else if (type == T_B) run_B<M, true>(a, x, y, sm, rt);
-      else run_C<M, true>(a, x, y, sm, rt);
     } else {
-      if (type == T_A) run_A<M>(a, x, y, sm, rt);
-      else if (type == T_B) run_B<M, false>(a, x, y, sm, rt);
-      else run_C<M, false>(a, x, y, sm, rt);
+      // `units` consecutive tiles or row groups; a barrier between them
+      // (each pass reuses the block's shared memory from the start)
+#pragma unroll 1
+      for (int u = 0; u < units; ++u) {
+        if (u) __syncthreads();
+        if constexpr (MODE == MODE_HERM) {
+          if (type == T_A) run_A_herm<M>(a, x, y + u, sm, rt);
+          else if (type == T_B) run_B_herm<M>(a, x, y + u, sm, rt);
+          else run_C_herm<M>(a, x, y + u, sm, rt);
+        } else if constexpr (MODE == MODE_TERN) {
+          if (type == T_A) run_A_tern<M>(a, x, y + u, sm, rt);
+          else if (type == T_B) run_B<M, true>(a, x, y + u, sm, rt);
+          else run_C<M, true>(a, x, y + u, sm, rt);
+        } else {
+          if (type == T_A) run_A<M>(a, x, y + u, sm, rt);
+          else if (type == T_B) run_B<M, false>(a, x, y + u, sm, rt);
+          else run_C<M, false>(a, x, y + u, sm, rt);
+        }
+      }
     }
   }
 }
@@ -823,6 +831,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
   // thread 0 takes the next queue index while the current task runs
   uint32_t next = 0;
   if (threadIdx.x == 0) next = atomicAdd(&a.hdr->counter, 1u);
+  long long t_end = clock64();   // thread 0: end of the previous task (start of the launch at first)
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -844,7 +853,8 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
     __syncthreads();
     const Task t = s_task;
     if (t.kc < 0 || !s_ok) break;
-    const int code = t.kc & 255, type = t.kc >> 8;
+    const int code = t.kc & 255, type = (t.kc >> 8) & 255, units = max(1, t.kc >> 16);
+    const long long t_got = clock64();
     if (code != cur) {
       // lo = zeta_TN^b (b < 2^sh), hi = zeta_TN^(a 2^sh), from the full table
       const int TN = (mode_tables_3m(MODE) ? 3 : 2) * size_of_code(code);
@@ -861,9 +871,13 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
       __syncthreads();
     }
     const long long t_start = clock64();
+    if (threadIdx.x == 0) {
+      atomicAdd(&a.hdr->handover_cycles, (unsigned long long)(t_got - t_end));
+      atomicAdd(&a.hdr->table_cycles, (unsigned long long)(t_start - t_got));
+    }
     switch (code) {
 #define DC_FX_CASE(c) \
-      case c: run_size<size_of_code(c), MODE>(&a, type, t.a, t.b, sm, rt); break;
+      case c: run_size<size_of_code(c), MODE>(&a, type, t.a, t.b, units, sm, rt); break;
       DC_FX_CASE(0) DC_FX_CASE(1) DC_FX_CASE(2) DC_FX_CASE(3) DC_FX_CASE(4) DC_FX_CASE(5)
       DC_FX_CASE(6) DC_FX_CASE(7) DC_FX_CASE(8) DC_FX_CASE(9) DC_FX_CASE(10)
       DC_FX_CASE(11) DC_FX_CASE(12) DC_FX_CASE(13) DC_FX_CASE(14) DC_FX_CASE(15)
@@ -877,9 +891,11 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
     if (threadIdx.x == 0) {
       // the barrier above orders every thread's stores of the task before
       // this release at GPU scope
-      if (t.sidx >= 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.cnt + t.sidx) : "memory");
+      if (t.sidx >= 0)
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(a.cnt + t.sidx), "r"(units) : "memory");
       // per-type time, for tracing where a launch spends its cycles
-      atomicAdd(&a.hdr->type_cycles[type & 3], (unsigned long long)(clock64() - t_start));
+      t_end = clock64();
+      atomicAdd(&a.hdr->type_cycles[type & 3], (unsigned long long)(t_end - t_start));
       atomicAdd(&a.hdr->type_count[type & 3], 1u);
     }
   }
@@ -1033,8 +1049,10 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
       const int c = big[l].first;
       const int nbc = mode == MODE_HERM ? tb.nbh[c] : tb.nb[c];
       const int cnt = type == T_B ? nbc : tb.na[c];
-      for (int u = 0; u < cnt; ++u) {
-        Task t{(type << 8) | c, l, u, -1, 0, -1};
+      const int grp = std::max(1, std::min(sc.units, kMaxUnits));
+      for (int u = 0; u < cnt; u += grp) {
+        const int n = std::min(grp, cnt - u);
+        Task t{(n << 16) | (type << 8) | c, l, u, -1, 0, -1};
         if (type == T_A) {
           if (k >= 4) { t.widx = 2 * n2 + (k - 4); t.wneed = batch_c[k - 4]; }
           t.sidx = 2 * l;

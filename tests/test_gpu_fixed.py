@@ -165,16 +165,40 @@ def test_schedules_give_identical_results(dc):
     ref = plan(tf, tg).clone()
     for target in (1, 7, 152):
         for mode in (0, 1, 2):
-            plan.set_schedule(target, mode)
-            assert plan.schedule() == (target, mode)
-            work = plan.workspace(tf.device)
-            h = plan(tf, tg, work=work)
-            torch.cuda.synchronize()
-            assert dc.read_status(work) == (0, 0)
-            assert torch.equal(h, ref), (target, mode)
+            for units in (1, 2, 4):
+                plan.set_task_units(units)
+                plan.set_schedule(target, mode)
+                assert plan.schedule() == (target, mode) and plan.task_units() == units
+                work = plan.workspace(tf.device)
+                h = plan(tf, tg, work=work)
+                torch.cuda.synchronize()
+                assert dc.read_status(work) == (0, 0)
+                assert torch.equal(h, ref), (target, mode, units)
     check_all(sizes, f, g, off, ref.cpu().numpy())
     other = dc.BatchedPlan(sizes + [48], dtype=torch.complex64)   # 48 < 64: runtime-shaped engine
-    assert other.schedule() is None
+    assert other.schedule() is None and other.task_units() is None
+    from paper_1008_1366_gb300 import api
+    with pytest.raises(api.DealiasError):
+        plan.set_task_units(5)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_task_units_for_every_mode(dc, dtype):
+    # several tiles or row groups per task: the trace counts units of work
+    # once per task, and the result does not change
+    sizes = [65536] * 2 + [640] * 20 + [64] * 130
+    plan, f, g, off, h1 = run_plan(dc, sizes, 36, dtype=dtype)
+    plan.set_task_units(4)
+    tf = torch.tensor(f, dtype=dtype, device="cuda")
+    tg = torch.tensor(g, dtype=dtype, device="cuda")
+    work = plan.workspace(tf.device)
+    h4 = plan(tf, tg, work=work)
+    torch.cuda.synchronize()
+    assert dc.read_status(work) == (0, 0)
+    assert np.array_equal(h4.cpu().numpy(), h1)
+    tr = dc.read_trace(work)
+    assert tr["tasks"] == {"L1": 3 + 3, "A": 8, "B": 16, "C": 8}, tr
+    check_all(sizes, f, g, off, h1, dtype)
 
 
 def test_bounded_wait_reports_timeout(dc):
