@@ -51,10 +51,14 @@ def parse():
     p.add_argument("--suite", action="store_true",
                    help="measure every configuration of the scope but the batched one, one JSON line each")
     p.add_argument("--suite-only", default=None,
-                   help="with --suite: only the configurations whose name contains this text "
-                        "(e.g. '3D Hermitian'; for profiling one of them)")
+                   help="with --suite: only the configurations whose name contains this text, "
+                        "'_' standing for a space (e.g. 3D_Hermitian; for profiling one of them)")
     p.add_argument("--no-suite", action="store_true",
                    help="leave the other configurations out of the headline line")
+    p.add_argument("--per-size", default=None,
+                   help="comma-separated sizes (or 'all' for the 31 of the workload): time one-size "
+                        "batches of about 16 M elements each on the fixed-shape engine, one JSON line "
+                        "per size (ps per element; for profiling one size alone)")
     p.add_argument("--instances", type=int, default=N_INST,
                    help="batch size (default 4096; smaller batches are for profiling only)")
     return p.parse_args()
@@ -316,7 +320,8 @@ def run_suite(args, only=None, peak=None):
     out = []
 
     def want(name):
-        return only is None or only in name
+        # `only` matches a name's text, '_' standing for a space
+        return only is None or only.replace("_", " ") in name
 
     def emit(name, ms, ts, nbytes, err, tol, pw=None, extra=None):
         T, sl, sh = one_sided_sigma(ts)
@@ -480,6 +485,28 @@ def run_suite(args, only=None, peak=None):
     return out
 
 
+def run_per_size(args):
+    """One-size batches of about 16 M elements (FP32, default queue order):
+    time per launch and ps per element, one JSON line per size.  Separates a
+    size's own cost from the cost of mixing sizes in one launch."""
+    import torch
+    import paper_1008_1366_gb300 as dcl
+    from paper_1008_1366_gb300 import synthetic
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sizes = synthetic.SIZES_31 if args.per_size == "all" else [int(x) for x in args.per_size.split(",")]
+    for m in sizes:
+        n = max(1, (1 << 24) // m)
+        f = torch.rand(n * m, dtype=torch.complex64, device=dev)
+        g = torch.rand(n * m, dtype=torch.complex64, device=dev)
+        plan = dcl.BatchedPlan([m] * n, dtype=torch.complex64)
+        out = torch.empty_like(f)
+        work = plan.workspace(dev)
+        ms, ts = _time_call(lambda: plan(f, g, out=out, work=work), max(3, args.steps), warm=max(3, args.warmup))
+        print(json.dumps({"m": m, "instances": n, "ms_median": ms, "ps_per_element": ms * 1e9 / (n * m),
+                          "level": plan.describe()[0][1]}), flush=True)
+        del f, g, out, work, plan
+
+
 def cufft_padded_context(ms, tf, tg, stream, reps=5):
     """Context only (not the product path): the conventional explicitly
     zero-padded convolution of the same batch on cuFFT through torch.fft,
@@ -524,6 +551,11 @@ def main():
         torch.cuda.set_device(local)
         for rec in run_suite(args, only=args.suite_only):
             print(json.dumps(rec), flush=True)
+        return
+    if args.per_size:
+        import torch
+        torch.cuda.set_device(local)
+        run_per_size(args)
         return
 
     import torch

@@ -52,7 +52,10 @@ def test_hermitian_dot2_1d(dc, m, dtype):
     check_parity(h.cpu().numpy(), oracle.dot_hermitian(fs, gs), dtype, 3 * m, dot_scale(fs, gs, True))
 
 
-@pytest.mark.parametrize("ms", [(1, 1), (3, 4), (8, 8), (16, 12), (64, 64), (9, 15), (2, 3, 4), (4, 4, 6)])
+# rows of 64 (and 2, 3, 64 in 3D) on the fixed engine's dot-product residues,
+# rows of 8192 (a two-level size) and other lengths on the runtime-shaped kernel
+@pytest.mark.parametrize("ms", [(1, 1), (3, 4), (8, 8), (16, 12), (64, 64), (9, 15), (2, 3, 4), (4, 4, 6),
+                                (3, 8192), (2, 3, 64)])
 @pytest.mark.parametrize("dtype", DT)
 def test_hermitian_dot2_nd(dc, ms, dtype):
     shape = synthetic.hermitian_shape(ms)
