@@ -18,10 +18,16 @@ LIB = os.path.join(HERE, "libdealias.so")
 
 SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu",
            "partition.cu", "pq.cu"]
-# the fixed-shape engine, one translation unit per precision
-FIXED = [(src, src.replace(".cu", f"_{tag}.o"), [f"-DDC_FX_P={ns}", f"-DDC_FX_C={c}"])
-         for src in ("fixed_batched.cu", "fixed_axis.cu")
-         for tag, ns, c in (("f", "f32", "float2"), ("d", "f64", "double2"))]
+# the fixed-shape engine per precision: the outer-axis kernels, the batched
+# planner, and the batched kernel of each convolution kind (MODE_* 0..4) in
+# a translation unit of its own, so that the kinds compile in parallel
+_PREC = (("f", "f32", "float2"), ("d", "f64", "double2"))
+FIXED = ([("fixed_axis.cu", f"fixed_axis_{tag}.o", [f"-DDC_FX_P={ns}", f"-DDC_FX_C={c}"]) for tag, ns, c in _PREC]
+         + [("fixed_batched.cu", f"fixed_batched_{tag}.o", [f"-DDC_FX_P={ns}", f"-DDC_FX_C={c}"])
+            for tag, ns, c in _PREC]
+         + [("fixed_batched.cu", f"fixed_batched_m{k}_{tag}.o", [f"-DDC_FX_P={ns}", f"-DDC_FX_C={c}",
+                                                                 f"-DDC_FX_MODE={k}"])
+            for k in range(5) for tag, ns, c in _PREC])
 # the fused 1D kernel, one translation unit per (kind, precision)
 INSTANCES = [(k, tag, c) for k in range(8) for tag, c in (("f", "float2"), ("d", "double2"))]
 
@@ -101,7 +107,7 @@ def build(verbose=False, jobs=None, extra_flags=()):
     units = _units()
     jobs = jobs or min(len(units), os.cpu_count() or 4)
     # longest units first: the fixed-shape engine, then the fused kernels
-    units.sort(key=lambda u: 0 if u[0] == "fixed_batched.cu" else (1 if u[0] == "conv1d_inst.cu" else 2))
+    units.sort(key=lambda u: 0 if "_m" in u[1] and u[0] == "fixed_batched.cu" else (1 if u[0] == "conv1d_inst.cu" else 2))
     with ThreadPoolExecutor(max_workers=jobs) as ex:
         results = list(ex.map(compile_one, units))
     objs = [o for o, _ in results]

@@ -50,6 +50,7 @@ struct dc_batched_plan {
   fx::L2Inst* d_l2 = nullptr;
   int64_t* d_l1tmp = nullptr;
   const void* tabs[fx::kNumSizes] = {};
+  const void* stabs[fx::kNumSizes] = {};   // stage-twiddle tables (null: none)
   size_t cnt_bytes = 0;   // header + counters, zeroed before each launch
   fx::Schedule fx_sched{0, 0};   // queue order of the fixed engine
   std::vector<int64_t> off_host;
@@ -76,11 +77,15 @@ struct FxOps {
   bool (*build_plan)(const int64_t*, int32_t, const int64_t*, const fx::Schedule&, int, fx::HostPlan*);
   dc_status (*prepare_kernel)(int, int*);
   dc_status (*launch)(const fx::FxArgs&, int, int, cudaStream_t);
+  void (*code_tabs)(int, int*, int*);
+  dc_status (*stage_tables)(int, const void**);
 };
-static const FxOps kFx32{fx::f32::size_code, fx::f32::code_size,   fx::f32::code_shape, fx::f32::code_smem,
-                         fx::f32::build_plan, fx::f32::prepare_kernel, fx::f32::launch};
-static const FxOps kFx64{fx::f64::size_code, fx::f64::code_size,   fx::f64::code_shape, fx::f64::code_smem,
-                         fx::f64::build_plan, fx::f64::prepare_kernel, fx::f64::launch};
+static const FxOps kFx32{fx::f32::size_code,      fx::f32::code_size,  fx::f32::code_shape, fx::f32::code_smem,
+                         fx::f32::build_plan,     fx::f32::prepare_kernel, fx::f32::launch, fx::f32::code_tabs,
+                         fx::f32::stage_tables};
+static const FxOps kFx64{fx::f64::size_code,      fx::f64::code_size,  fx::f64::code_shape, fx::f64::code_smem,
+                         fx::f64::build_plan,     fx::f64::prepare_kernel, fx::f64::launch, fx::f64::code_tabs,
+                         fx::f64::stage_tables};
 
 namespace {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -232,7 +237,11 @@ fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void*
   auto aliases = [&](const void* o) { return o && (o == f || o == g || o == e || o == e2); };
   a.in_place = (aliases(h) || aliases(h2)) ? 1 : 0;
   a.wait_limit = fx::kWaitLimit;
-  for (int c = 0; c < fx::kNumSizes; ++c) a.tab[c] = p->tabs[c];
+  for (int c = 0; c < fx::kNumSizes; ++c) {
+    a.tab[c] = p->tabs[c];
+    a.stab[c] = p->stabs[c];
+    if (p->stabs[c]) p->ops->code_tabs(c, &a.stab_n[c], &a.stab_off[c]);
+  }
   return a;
 }
 
@@ -344,6 +353,8 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
     st = get_root_table((fx::mode_tables_3m(mode) ? 3 : 2) * p->ops->code_size(c), p->ds, &tw);
     if (st != DC_OK) return st;
     p->tabs[c] = tw;
+    st = p->ops->stage_tables(c, &p->stabs[c]);
+    if (st != DC_OK) return st;
   }
   st = fx_upload(p, off);
   if (st != DC_OK) return st;

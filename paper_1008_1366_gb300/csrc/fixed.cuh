@@ -139,6 +139,98 @@ template <int L, int E, int S, bool FWD> struct Stage {
 };
 
 // ---------------------------------------------------------------------------
+// stage-twiddle tables.  Stage s of a transform multiplies input q of the
+// butterfly at j by zeta_{Ns R}^{q k}, k = j mod Ns.  For every twiddled
+// stage with Ns R <= kTabP the engine keeps these factors in shared memory
+// as a table of R - 1 rows of Ns entries (row q - 1, column k), filled from
+// the root table when a block switches to a size: one load per factor
+// instead of forming the powers of zeta_{Ns R}^k by products, and the
+// threads of a warp read consecutive (or equal) entries of a row, so the
+// loads meet no bank conflicts.  The tables of a transform (L, E) list its
+// distinct (Ns, R) over both directions (the forward transform runs the
+// radices in reverse order).
+// ---------------------------------------------------------------------------
+constexpr int kTabP = 512;
+struct TabLayout {
+  int n;
+  int ns[24], r[24], off[24];
+  int total;   // entries
+};
+// Shared memory a block may use: two blocks per SM in FP32, one in FP64
+// (228 KB per SM less 1 KB reserved per block and the static variables).
+constexpr int kBlockSmemMax = kDouble ? 233472 - 1024 - 64 : (233472 - 2 * 1024) / 2 - 64;
+template <int L, int E> struct StageTab {
+  // A one-level transform (L, E) of the batched kernel takes its whole block:
+  // kThreads / (L / E) instances in padded shared arrays behind the root
+  // reservation.  Its tables go behind those, and are left out (the
+  // twiddles formed by products instead) where they would not fit.
+  static constexpr bool fits(int total) {
+    return !(E == family_E(L) && is_level1(L)) ||
+           kRootsMax * (int)sizeof(C) + (kThreads / (L / E)) * group_stride(L, L / E) * (int)sizeof(C) + 16 +
+                   total * (int)sizeof(C) <=
+               kBlockSmemMax;
+  }
+  static constexpr TabLayout make() {
+    TabLayout t{};
+    using F = Fft<L, E>;
+    for (int d = 0; d < 2; ++d)
+      for (int s = 1; s < F::n; ++s) {
+        const int ns = F::ns(d == 1, s), r = F::radix(d == 1, s);
+        if (ns * r > kTabP) continue;
+        bool seen = false;
+        for (int x = 0; x < t.n; ++x) seen = seen || (t.ns[x] == ns && t.r[x] == r);
+        if (seen) continue;
+        t.ns[t.n] = ns;
+        t.r[t.n] = r;
+        t.off[t.n] = t.total;
+        t.total += (r - 1) * ns;
+        ++t.n;
+      }
+    if (!fits(t.total)) t = TabLayout{};
+    return t;
+  }
+  static constexpr TabLayout lay = make();
+  // entry offset of the table of (Ns, R), -1 when the stage has none
+  static constexpr int find(int ns, int r) {
+    for (int x = 0; x < lay.n; ++x)
+      if (lay.ns[x] == ns && lay.r[x] == r) return lay.off[x];
+    return -1;
+  }
+};
+
+// The root tables plus the stage tables of one transform (st: its first
+// entry).  Code given a plain Roots<C> forms every stage twiddle from the
+// root table instead.
+struct TabRoots : Roots<C> {
+  const C* st;
+};
+template <class RT, int L, int E, int NS, int R> struct TabOf {
+  static constexpr int off = -1;
+};
+template <int L, int E, int NS, int R> struct TabOf<TabRoots, L, E, NS, R> {
+  static constexpr int off = StageTab<L, E>::find(NS, R);
+};
+
+// Writes the stage tables of transform (L, E) at st (device memory; one
+// block of kThreads threads): zeta_{Ns R}^{q k} computed in FP64 with
+// sincospi from the exponent q k mod Ns R, then rounded.
+template <int L, int E>
+__device__ __forceinline__ void gen_stage_tabs(C* st) {
+  constexpr TabLayout t = StageTab<L, E>::lay;
+#pragma unroll
+  for (int x = 0; x < t.n; ++x) {
+    const int ns = t.ns[x], p = ns * t.r[x];
+    for (int e = threadIdx.x; e < (t.r[x] - 1) * ns; e += kThreads) {
+      const int q = 1 + e / ns, k = e - (q - 1) * ns;
+      double sn, cs;
+      sincospi(2.0 * (double)((q * k) % p) / (double)p, &sn, &cs);
+      st[t.off[x] + e].x = (Real)cs;
+      st[t.off[x] + e].y = (Real)sn;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // compound radices R = A B (12 = 4 x 3, 20 = 4 x 5, 24 = 8 x 3) as nested
 // DFTs in registers: with n = B n1 + n2 and k = k1 + A k2,
 //   X[k1 + A k2] = sum_{n2} zeta_B^{n2 k2} zeta_R^{n2 k1} sum_{n1} zeta_A^{n1 k1} x[B n1 + n2]
@@ -321,16 +413,28 @@ __device__ __forceinline__ void tw_apply(C* x, const Roots<C>& rt, int e) {
 
 // twiddles zeta_{Ns R}^{+-q k} (root table of zeta_TN) and the radix-R DFT
 // of each butterfly; backward: +, forward: -
-template <int L, int E, int S, bool FWD, int TN>
-__device__ __forceinline__ void dft(C* v, int i, const Roots<C>& rt) {
+template <int L, int E, int S, bool FWD, int TN, class RT>
+__device__ __forceinline__ void dft(C* v, int i, const RT& rt) {
   using K = Stage<L, E, S, FWD>;
   constexpr int sgn = FWD ? -1 : 1;
+  constexpr int toff = K::Ns > 1 ? TabOf<RT, L, E, K::Ns, K::R>::off : -1;
 #pragma unroll
   for (int b = 0; b < K::NB; ++b) {
     if constexpr (K::Ns > 1) {
       static_assert(TN % (K::Ns * K::R) == 0, "root table must cover the stage");
       const int j = i + b * K::T;
-      tw_apply<K::R, FWD>(&v[b * K::R], rt, (j % K::Ns) * (TN / (K::Ns * K::R)));
+      if constexpr (toff >= 0) {
+        // row q - 1 of the stage table, column k = j mod Ns
+        const C* t = rt.st + toff + j % K::Ns;
+        C* x = &v[b * K::R];
+#pragma unroll
+        for (int q = 1; q < K::R; ++q) {
+          const C w = t[(q - 1) * K::Ns];
+          x[q] = FWD ? cmulc(x[q], w) : cmul(x[q], w);
+        }
+      } else {
+        tw_apply<K::R, FWD>(&v[b * K::R], rt, (j % K::Ns) * (TN / (K::Ns * K::R)));
+      }
     }
     rdft_fx<K::R>(&v[b * K::R], sgn);
   }
@@ -350,9 +454,9 @@ __device__ __forceinline__ int pos(int i, int b, int q) {
 // transform's output at natural index x (e: its register index).  A and B: padded shared arrays of
 // the group.  Every thread of the block calls this (barriers inside).
 // ---------------------------------------------------------------------------
-template <int L, int E, int TN, int S, class Sy>
+template <int L, int E, int TN, int S, class RT, class Sy>
 __device__ __forceinline__ void bwd_middle(C* v, int i, bool act, const Contig& A, const Contig& B,
-                                           const Roots<C>& rt, const Sy& sync) {
+                                           const RT& rt, const Sy& sync) {
   constexpr int n = Fft<L, E>::n;
   if constexpr (S < n - 1) {
     if (act) {
@@ -372,8 +476,8 @@ __device__ __forceinline__ void bwd_middle(C* v, int i, bool act, const Contig& 
 }
 
 // middle stages of one array in place (gather, barrier, scatter, barrier)
-template <int L, int E, int TN, bool FWD, int S, class Lay, class Sy>
-__device__ __forceinline__ void one_middle(C* v, int i, bool act, const Lay& A, const Roots<C>& rt,
+template <int L, int E, int TN, bool FWD, int S, class Lay, class RT, class Sy>
+__device__ __forceinline__ void one_middle(C* v, int i, bool act, const Lay& A, const RT& rt,
                                            const Sy& sync) {
   constexpr int n = Fft<L, E>::n;
   if constexpr (S < n - 1) {
@@ -393,8 +497,8 @@ struct CProd {
   __device__ __forceinline__ C operator()(C a, C b) const { return cmul(a, b); }
 };
 
-template <int L, int E, int TN, class Ld, class St, class Sy, class Pr = CProd>
-__device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, const Roots<C>& rt,
+template <int L, int E, int TN, class RT, class Ld, class St, class Sy, class Pr = CProd>
+__device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, const RT& rt,
                                              const Ld& ld, const St& st, const Sy& sync,
                                              const Pr& prod = Pr{}) {
   using F = Fft<L, E>;
@@ -460,8 +564,8 @@ __device__ __forceinline__ void conv_residue(int i, bool act, C* Ap, C* Bp, cons
 // their product, a real array, takes one forward transform.  ld(x, e) gives
 // the packed input at natural index x; st(x, e, v) takes the output.
 // ---------------------------------------------------------------------------
-template <int L, int E, int TN, class Ld, class St, class Sy>
-__device__ __forceinline__ void conv1_residue(int i, C* Ap, const Roots<C>& rt, const Ld& ld, const St& st,
+template <int L, int E, int TN, class RT, class Ld, class St, class Sy>
+__device__ __forceinline__ void conv1_residue(int i, C* Ap, const RT& rt, const Ld& ld, const St& st,
                                               const Sy& sync) {
   using F = Fft<L, E>;
   constexpr int n = F::n;
@@ -512,8 +616,8 @@ __device__ __forceinline__ void conv1_residue(int i, C* Ap, const Roots<C>& rt, 
 // (Y_k - conj Y_{L-k}) / 2i, read back through A.  ld(x, arr, e) gives
 // input arr at natural index x; st(x, e, v, o) takes output o.
 // ---------------------------------------------------------------------------
-template <int L, int E, int TN, class Ld, class St, class Sy>
-__device__ __forceinline__ void conv_pair_residue(int i, C* Ap, C* Bp, const Roots<C>& rt, const Ld& ld,
+template <int L, int E, int TN, class RT, class Ld, class St, class Sy>
+__device__ __forceinline__ void conv_pair_residue(int i, C* Ap, C* Bp, const RT& rt, const Ld& ld,
                                                   const St& st, const Sy& sync) {
   using F = Fft<L, E>;
   constexpr int n = F::n;
@@ -584,8 +688,8 @@ __device__ __forceinline__ void conv_pair_residue(int i, C* Ap, C* Bp, const Roo
 // inputs of stage 0 in gather order; st(x, e, v) takes output x (register e).  D: this
 // thread's column of the interleaved tile.  Every thread calls this.
 // ---------------------------------------------------------------------------
-template <int L, int E, int W, int TN, bool FWD, class St>
-__device__ __forceinline__ void column(C* v, int i, C* Dp, const Roots<C>& rt, const St& st) {
+template <int L, int E, int W, int TN, bool FWD, class RT, class St>
+__device__ __forceinline__ void column(C* v, int i, C* Dp, const RT& rt, const St& st) {
   constexpr int n = Fft<L, E>::n;
   static_assert(n >= 2, "at least two stages");
   const Inter<W> D{Dp};

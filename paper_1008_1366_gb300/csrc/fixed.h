@@ -77,6 +77,11 @@ struct FxArgs {
   int32_t mode;            // MODE_*
   long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
   const void* tab[kNumSizes];     // root tables zeta_{2m}^i, i < 2m, per size code
+  // stage-twiddle tables per size code (null for sizes without): stab_n
+  // entries, copied to byte stab_off of the block's shared memory
+  const void* stab[kNumSizes];
+  int32_t stab_n[kNumSizes];
+  int32_t stab_off[kNumSizes];
 };
 
 struct HostPlan {
@@ -115,6 +120,11 @@ constexpr long long kWaitLimit = 1ll << 32;   // about two seconds at 2 GHz
   void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W);           \
   /* dynamic shared memory the kernel needs for a size code */                              \
   int code_smem(int code);                                                                  \
+  /* stage-twiddle tables of a size code: entries and their shared-memory byte offset */    \
+  void code_tabs(int code, int* entries, int* byte_off);                                    \
+  /* the stage-twiddle tables of a size code in device memory (generated once per */      \
+  /* device in FP64, rounded); null when the size has none */                              \
+  dc_status stage_tables(int code, const void** out);                                       \
   /* the task queue for n instances of sizes m[i] at element offsets off[i] for a */      \
   /* convolution kind (MODE_*: row tasks and partial-output slots per instance) */         \
   bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule& sc,     \

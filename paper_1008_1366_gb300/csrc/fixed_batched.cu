@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -104,7 +105,16 @@ template <int M> struct Shape {
   static constexpr int herm_lo = 1 << roots_sh(3 * M);
   static constexpr bool herm_behind = !l1 && herm_roots > kRootsMax;
   static constexpr int herm_off = kRootsMax * CB + (smem + 15) / 16 * 16;   // bytes from the start
-  static constexpr int total = kRootsMax * CB + smem + (herm_behind ? 16 + (herm_roots - herm_lo) * CB : 0);
+  static constexpr int base = kRootsMax * CB + smem + (herm_behind ? 16 + (herm_roots - herm_lo) * CB : 0);
+  // Stage-twiddle tables (fixed.cuh), behind everything else: those of the
+  // rows (L1, E1), then those of the columns (L2, EC) unless the two
+  // transforms are the same; none for one-level sizes.
+  static constexpr bool tab_same = !l1 && L1 == L2 && E1 == EC;
+  static constexpr int tab_col = (l1 || tab_same) ? 0 : StageTab<L1, E1>::lay.total;
+  static constexpr int tab_entries =
+      l1 ? 0 : tab_col + (tab_same ? StageTab<L1, E1>::lay.total : StageTab<L2, EC>::lay.total);
+  static constexpr int tab_off = (base + 15) / 16 * 16;   // bytes from the start
+  static constexpr int total = tab_off + tab_entries * CB;
   static_assert(herm_lo <= kRootsMax, "low root table fits its reservation");
   static_assert(roots_count(2 * M) <= kRootsMax && (!l1 || herm_roots <= kRootsMax), "root tables fit");
   // FP32: two blocks per SM, FP64: one (228 KB per SM less 1 KB reserved per
@@ -115,6 +125,26 @@ template <int M> struct Shape {
 // ---------------------------------------------------------------------------
 // device side
 // ---------------------------------------------------------------------------
+
+// One-level transforms form their stage twiddles by products; the row and
+// column transforms of two-level sizes read their stage tables, which sit
+// at a fixed place of the block's dynamic shared memory (so their address
+// is a constant, not a register held across the task).
+extern __shared__ __align__(16) unsigned char fx_smem[];
+template <int M> __device__ __forceinline__ TabRoots row_roots(const Roots<C>& r) {
+  return TabRoots{r, (const C*)(fx_smem + Shape<M>::tab_off)};
+}
+template <int M> __device__ __forceinline__ TabRoots col_roots(const Roots<C>& r) {
+  return TabRoots{r, (const C*)(fx_smem + Shape<M>::tab_off) + Shape<M>::tab_col};
+}
+template <int M> __device__ __forceinline__ void gen_size_tabs(C* st) {
+  using S = Shape<M>;
+  if constexpr (!S::l1) {
+    gen_stage_tabs<S::L1, S::E1>(st);
+    if constexpr (!S::tab_same) gen_stage_tabs<S::L2, S::EC>(st + S::tab_col);
+  }
+}
+
 
 // Residue r of a centered Hermitian convolution (Sec. 2.3, N = 3m), in a
 // form without branches on r or k, so that the loads of all E elements of
@@ -428,7 +458,7 @@ __device__ __noinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, Root
       for (int e = 0; e < E; ++e) v[e] = r ? cmul(raw[e], tw[e]) : raw[e];
       // S[j2][k1]; the factor zeta_m^{j2 k1} is applied in pass B
       C* dst = scr + (size_t)(2 * r + arr) * M + k1;
-      column<L2, E, W, TN, false>(v, i, sm + c, rt, [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
+      column<L2, E, W, TN, false>(v, i, sm + c, col_roots<M>(rt), [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
       __syncthreads();
     }
   }
@@ -505,7 +535,7 @@ __device__ __noinline__ void run_A_tern(const FxArgs* a, int l, int tile, C* sm,
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = r ? cmul(raw[e], tw[e]) : raw[e];
       C* dst = scr + (size_t)(2 * r + arr) * M + k1;
-      column<L2, E, W, TN, false>(v, i, sm + c, rt, [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
+      column<L2, E, W, TN, false>(v, i, sm + c, col_roots<M>(rt), [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
       __syncthreads();
     }
   }
@@ -543,7 +573,7 @@ __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Root
   static_assert(E1 <= 20, "rows hold their twiddles in registers");
   C tw[E1];
   conv_residue<L1, E1, TN>(
-      i, true, A, B, rt,
+      i, true, A, B, row_roots<M>(rt),
       [&](int x, int arr, int e) {
         if (arr == 0) tw[e] = rt.at(2 * j2 * x);
         return cmul(__ldcg((arr ? sg : (const C*)sf) + x), tw[e]);
@@ -578,9 +608,9 @@ __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Root
 #pragma unroll
       for (int q = 0; q < K::R; ++q) vin[r][b * K::R + q] = __ldcg(src + (size_t)L1 * pos<L2, E, 0, true>(i, b, q));
   }
-  column<L2, E, W, TN, true>(vin[0], i, sm + c, rt, [&](int, int e, C y) { y0[e] = y; });
+  column<L2, E, W, TN, true>(vin[0], i, sm + c, col_roots<M>(rt), [&](int, int e, C y) { y0[e] = y; });
   __syncthreads();
-  column<L2, E, W, TN, true>(vin[1], i, sm + c, rt, [&](int k2, int e, C y) {
+  column<L2, E, W, TN, true>(vin[1], i, sm + c, col_roots<M>(rt), [&](int k2, int e, C y) {
     const int k = k1 + L1 * k2;
     if (!TERN || 2 * k2 < L2) h[(size_t)L1 * k2] = cscale(cadd(y0[e], cmulc(y, rt.at(k))), sc);
   });
@@ -648,7 +678,7 @@ __device__ __noinline__ void run_A_herm(const FxArgs* a, int l, int tile, C* sm,
       }
     // S_r[j2][k1]; the factor zeta_m^{j2 k1} is applied in pass B
     C* dst = scr + (size_t)ri * M + k1;
-    column<L2, E, W, TN, false>(v, i, sm + c, rt, [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
+    column<L2, E, W, TN, false>(v, i, sm + c, col_roots<M>(rt), [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
     __syncthreads();
   }
 }
@@ -669,7 +699,7 @@ __device__ __noinline__ void run_B_herm(const FxArgs* a, int l, int unit, C* sm,
   static_assert(E1 <= 20, "rows hold their twiddles in registers");
   C tw[E1];
   conv1_residue<L1, E1, TN>(
-      i, sm + gi * GS, rt,
+      i, sm + gi * GS, row_roots<M>(rt),
       [&](int x, int e) {
         tw[e] = rt.at(3 * j2 * x);
         return cmul(__ldcg(s + x), tw[e]);
@@ -701,7 +731,7 @@ __device__ __noinline__ void run_C_herm(const FxArgs* a, int l, int tile, C* sm,
     for (int b = 0; b < K::NB; ++b)
 #pragma unroll
       for (int q = 0; q < K::R; ++q) v[b * K::R + q] = __ldcg(src + (size_t)L1 * pos<L2, E, 0, true>(i, b, q));
-    column<L2, E, W, TN, true>(v, i, sm + c, rt, [&](int k2, int e, C y) {
+    column<L2, E, W, TN, true>(v, i, sm + c, col_roots<M>(rt), [&](int k2, int e, C y) {
       if (r != 0) {
         const C t = rt.at(k1 + L1 * k2);
         y = r > 0 ? cmulc(y, t) : cmul(y, t);
@@ -821,7 +851,7 @@ __device__ __forceinline__ int roots_off_of(int code, bool herm) {
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid_constant__ FxArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem_raw = fx_smem;
   C* rts = (C*)smem_raw;
   C* sm = rts + kRootsMax;
   __shared__ Task s_task;
@@ -864,8 +894,13 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
       // or sits behind the task data for the Hermitian level-2 sizes
       const int hoff = roots_off_of(code, mode_tables_3m(MODE));
       C* hi = hoff ? (C*)(smem_raw + hoff) : rts + nlo;
-      for (int e = threadIdx.x; e < cnt; e += kThreads)
-        (e < nlo ? rts[e] : hi[e - nlo]) = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
+      // and the size's stage tables (a contiguous copy) behind its task data
+      const C* stab = (const C*)a.stab[code];
+      C* sdst = (C*)(smem_raw + a.stab_off[code]);
+      for (int e = threadIdx.x; e < cnt + a.stab_n[code]; e += kThreads) {
+        if (e < cnt) (e < nlo ? rts[e] : hi[e - nlo]) = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
+        else sdst[e - cnt] = __ldg(stab + (e - cnt));
+      }
       rt = Roots<C>{rts, hi, sh, nlo - 1};
       cur = code;
       __syncthreads();
@@ -904,6 +939,36 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// Each kind's kernel is compiled in a translation unit of its own (built with
+// DC_FX_MODE set), so the kinds compile in parallel; the planner below is
+// built once, without DC_FX_MODE, and reaches the kernels through these.
+dc_status prepare_mode0(int smem, int* blocks);
+dc_status prepare_mode1(int smem, int* blocks);
+dc_status prepare_mode2(int smem, int* blocks);
+dc_status prepare_mode3(int smem, int* blocks);
+dc_status prepare_mode4(int smem, int* blocks);
+dc_status launch_mode0(const FxArgs& a, int grid, int smem, cudaStream_t s);
+dc_status launch_mode1(const FxArgs& a, int grid, int smem, cudaStream_t s);
+dc_status launch_mode2(const FxArgs& a, int grid, int smem, cudaStream_t s);
+dc_status launch_mode3(const FxArgs& a, int grid, int smem, cudaStream_t s);
+dc_status launch_mode4(const FxArgs& a, int grid, int smem, cudaStream_t s);
+
+#if defined(DC_FX_MODE)
+#define DC_FX_CAT2(a, b) a##b
+#define DC_FX_CAT(a, b) DC_FX_CAT2(a, b)
+dc_status DC_FX_CAT(prepare_mode, DC_FX_MODE)(int smem, int* blocks) {
+  DC_CUDA_TRY(cudaFuncSetAttribute(fx_kernel<DC_FX_MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  DC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fx_kernel<DC_FX_MODE>, kThreads, smem));
+  return DC_OK;
+}
+dc_status DC_FX_CAT(launch_mode, DC_FX_MODE)(const FxArgs& a, int grid, int smem, cudaStream_t s) {
+  fx_kernel<DC_FX_MODE><<<grid, kThreads, smem, s>>>(a);
+  DC_CUDA_TRY(cudaGetLastError());
+  return DC_OK;
+}
+#undef DC_FX_CAT
+#undef DC_FX_CAT2
+#else
 namespace {
 template <int... Cs> struct CodeTable {
   static void fill(int* lvl, int* per, int* l1, int* l2, int* w, int* na, int* nb, int* nbh, int* smem) {
@@ -915,14 +980,27 @@ template <int... Cs> struct CodeTable {
       smem[k] = Shape<size_of_code(Cs)>::total, ++k), ...);
   }
 };
+template <int... Cs> struct TabTable {
+  static void fill(int* n, int* off) {
+    int k = 0;
+    ((n[k] = Shape<size_of_code(Cs)>::tab_entries, off[k] = Shape<size_of_code(Cs)>::tab_off, ++k), ...);
+  }
+};
 struct Tables {
   int lvl[kNumSizes], per[kNumSizes], l1[kNumSizes], l2[kNumSizes], w[kNumSizes], na[kNumSizes],
-      nb[kNumSizes], nbh[kNumSizes], smem[kNumSizes];
+      nb[kNumSizes], nbh[kNumSizes], smem[kNumSizes], tabn[kNumSizes], taboff[kNumSizes];
   Tables() {
     CodeTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
               26, 27, 28, 29, 30>::fill(lvl, per, l1, l2, w, na, nb, nbh, smem);
+    TabTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26,
+             27, 28, 29, 30>::fill(tabn, taboff);
   }
 };
+
+// the stage tables of a size, one block
+template <int M> __global__ void gen_tabs_kernel(C* st) { gen_size_tabs<M>(st); }
+std::mutex g_tab_mu;
+std::map<std::pair<int, int>, void*> g_stage_tabs;   // (device, size code) -> tables
 const Tables& tables() {
   static Tables t;
   return t;
@@ -937,6 +1015,55 @@ int size_code(int64_t m) {
 int64_t code_size(int code) { return size_of_code(code); }
 bool code_level1(int code) { return tables().lvl[code] == 1; }
 int code_smem(int code) { return tables().smem[code]; }
+void code_tabs(int code, int* entries, int* byte_off) {
+  *entries = tables().tabn[code];
+  *byte_off = tables().taboff[code];
+}
+
+dc_status stage_tables(int code, const void** out) {
+  *out = nullptr;
+  const int n = tables().tabn[code];
+  if (n == 0) return DC_OK;
+  int dev = 0;
+  DC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_tab_mu);
+  auto it = g_stage_tabs.find({dev, code});
+  if (it != g_stage_tabs.end()) {
+    *out = it->second;
+    return DC_OK;
+  }
+  void* p = nullptr;
+  DC_CUDA_TRY(cudaMalloc(&p, (size_t)n * sizeof(C)));
+  cudaStream_t s;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    dc_set_last_cuda_error(e);
+    return DC_ERR_CUDA;
+  }
+  switch (code) {
+#define DC_FX_GEN(c) \
+    case c: gen_tabs_kernel<size_of_code(c)><<<1, kThreads, 0, s>>>((C*)p); break;
+    DC_FX_GEN(0) DC_FX_GEN(1) DC_FX_GEN(2) DC_FX_GEN(3) DC_FX_GEN(4) DC_FX_GEN(5) DC_FX_GEN(6) DC_FX_GEN(7)
+    DC_FX_GEN(8) DC_FX_GEN(9) DC_FX_GEN(10) DC_FX_GEN(11) DC_FX_GEN(12) DC_FX_GEN(13) DC_FX_GEN(14)
+    DC_FX_GEN(15) DC_FX_GEN(16) DC_FX_GEN(17) DC_FX_GEN(18) DC_FX_GEN(19) DC_FX_GEN(20) DC_FX_GEN(21)
+    DC_FX_GEN(22) DC_FX_GEN(23) DC_FX_GEN(24) DC_FX_GEN(25) DC_FX_GEN(26) DC_FX_GEN(27) DC_FX_GEN(28)
+    DC_FX_GEN(29) DC_FX_GEN(30)
+#undef DC_FX_GEN
+    default: break;
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    dc_set_last_cuda_error(e);
+    return DC_ERR_CUDA;
+  }
+  g_stage_tabs[{dev, code}] = p;
+  *out = p;
+  return DC_OK;
+}
 void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W) {
   const Tables& t = tables();
   *level = t.lvl[code];
@@ -1094,11 +1221,10 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
 
 dc_status prepare_kernel(int smem, int* blocks_per_sm) {
   int bmin = 1 << 20;
-  for (auto k : {fx_kernel<MODE_COMPLEX>, fx_kernel<MODE_HERM>, fx_kernel<MODE_TERN>, fx_kernel<MODE_PAIR>,
-                 fx_kernel<MODE_HDOT2>}) {
-    DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  for (auto prep : {prepare_mode0, prepare_mode1, prepare_mode2, prepare_mode3, prepare_mode4}) {
     int b = 0;
-    DC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kThreads, smem));
+    const dc_status st = prep(smem, &b);
+    if (st != DC_OK) return st;
     bmin = std::min(bmin, b);
   }
   if (bmin < 1) return DC_ERR_SIZE;
@@ -1108,16 +1234,15 @@ dc_status prepare_kernel(int smem, int* blocks_per_sm) {
 
 dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s) {
   switch (a.mode) {
-    case MODE_COMPLEX: fx_kernel<MODE_COMPLEX><<<grid, kThreads, smem, s>>>(a); break;
-    case MODE_HERM: fx_kernel<MODE_HERM><<<grid, kThreads, smem, s>>>(a); break;
-    case MODE_TERN: fx_kernel<MODE_TERN><<<grid, kThreads, smem, s>>>(a); break;
-    case MODE_PAIR: fx_kernel<MODE_PAIR><<<grid, kThreads, smem, s>>>(a); break;
-    case MODE_HDOT2: fx_kernel<MODE_HDOT2><<<grid, kThreads, smem, s>>>(a); break;
+    case MODE_COMPLEX: return launch_mode0(a, grid, smem, s);
+    case MODE_HERM: return launch_mode1(a, grid, smem, s);
+    case MODE_TERN: return launch_mode2(a, grid, smem, s);
+    case MODE_PAIR: return launch_mode3(a, grid, smem, s);
+    case MODE_HDOT2: return launch_mode4(a, grid, smem, s);
     default: return DC_ERR_ARG;
   }
-  DC_CUDA_TRY(cudaGetLastError());
-  return DC_OK;
 }
+#endif  // DC_FX_MODE
 
 }  // namespace DC_FX_P
 }  // namespace fx
