@@ -55,6 +55,8 @@ def parse():
                         "'_' standing for a space (e.g. 3D_Hermitian; for profiling one of them)")
     p.add_argument("--no-suite", action="store_true",
                    help="leave the other configurations out of the headline line")
+    p.add_argument("--variants", default=None,
+                   help="with --per-size: split-variant mask of the two-level sizes (e.g. 0xffffffff)")
     p.add_argument("--per-size", default=None,
                    help="comma-separated sizes (or 'all' for the 31 of the workload): time one-size "
                         "batches of about 16 M elements each on the fixed-shape engine, one JSON line "
@@ -499,11 +501,14 @@ def run_per_size(args):
         f = torch.rand(n * m, dtype=torch.complex64, device=dev)
         g = torch.rand(n * m, dtype=torch.complex64, device=dev)
         plan = dcl.BatchedPlan([m] * n, dtype=torch.complex64)
+        if args.variants:
+            plan.set_variants(int(args.variants, 0))
         out = torch.empty_like(f)
         work = plan.workspace(dev)
         ms, ts = _time_call(lambda: plan(f, g, out=out, work=work), max(3, args.steps), warm=max(3, args.warmup))
+        d = plan.describe()[0]
         print(json.dumps({"m": m, "instances": n, "ms_median": ms, "ps_per_element": ms * 1e9 / (n * m),
-                          "level": plan.describe()[0][1]}), flush=True)
+                          "level": d[1], "split": "%dx%d" % (d[3], d[4]) if d[1] == 2 else None}), flush=True)
         del f, g, out, work, plan
 
 
@@ -778,7 +783,9 @@ def main():
                                        f"(cost m log2 m), no collective on the data path"),
                        "partition_max_over_mean_load": max(loads) / (sum(loads) / world),
                        "schedule": {"batch_target_tiles": plan.schedule()[0], "l1_placement": plan.schedule()[1],
-                                    "task_units": plan.task_units()}},
+                                    "task_units": plan.task_units(), "split_variant_mask": plan.variants(),
+                                    "two_level_splits": {str(d[0]): "%dx%d" % (d[3], d[4])
+                                                         for d in plan.describe() if d[1] == 2}}},
             "roofline": roof,
             "step_ms_stats": {"mean": T_mean, "sigma_L": sig_l, "sigma_H": sig_h, "median": statistics.median(per)},
             "cpu_baseline": cpu,

@@ -333,6 +333,24 @@ dc_status dc_batched_plan_set_schedule(dc_batched_plan* plan, int32_t batch_targ
  * plans or values. */
 dc_status dc_batched_plan_task_units(const dc_batched_plan* plan, int32_t* units);
 dc_status dc_batched_plan_set_task_units(dc_batched_plan* plan, int32_t units);
+/* Split variants of the two-level sizes of such a plan (FP32 plans; no
+ * counterpart in the paper: a tile-shape choice of this engine).  A size m of
+ * the set above 2^12 (3*2^11, 5*2^10) runs its m-point sub-transforms as
+ * L1-point rows and L2-point columns, m = L1 * L2; variant 0 takes L2 = 128
+ * up to m = 32768 and 256 above, variant 1 the other of the two, which
+ * changes the row length, the threads per row and the column tile width.
+ * Bit c of *mask is set when the size with size code c (the position of m
+ * in 64, 128, ..., 65536, 96, ..., 49152, 80, ..., 40960) runs variant 1;
+ * dc_batched_plan_describe reports the resulting L1, L2 and tile width.
+ * DC_PLAN_AUTOTUNE times both variants of every such size of the plan on
+ * that size's instances alone and keeps variant 1 where it is faster by at
+ * least 1 %.  _set_ rebuilds the queue with the given mask (bits of sizes
+ * without a second variant, and every bit of FP64 plans, are ignored; the
+ * result does not depend on it, only the time does; query the workspace
+ * size again; not while a launch of the plan is in flight).  DC_ERR_ARG for
+ * plans off the fixed-shape engine or in the one-per-launch mode. */
+dc_status dc_batched_plan_variants(const dc_batched_plan* plan, uint32_t* mask);
+dc_status dc_batched_plan_set_variants(dc_batched_plan* plan, uint32_t mask);
 dc_status dc_conv_complex_1d_batched(const dc_batched_plan* plan, const void* f, const void* g,
                                      void* h, void* work, size_t work_bytes, void* stream);
 /* Failure-path self-test, no counterpart in the paper: launches the

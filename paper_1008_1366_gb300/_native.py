@@ -52,6 +52,8 @@ SIGNATURES = {
     "dc_batched_plan_set_schedule": [_vp, _i32, _i32],
     "dc_batched_plan_task_units": [_vp, ctypes.POINTER(_i32)],
     "dc_batched_plan_set_task_units": [_vp, _i32],
+    "dc_batched_plan_variants": [_vp, ctypes.POINTER(ctypes.c_uint32)],
+    "dc_batched_plan_set_variants": [_vp, ctypes.c_uint32],
     "dc_selftest_wait_timeout": [_vp, _sz, _i64, _vp],
     "dc_read_trace": [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)],
     "dc_batched_plan_host_workspace_size": [_vp, _i32, ctypes.POINTER(_sz)],

@@ -357,6 +357,24 @@ class BatchedPlan:
         self.workspace_bytes = int(ws.value)
         self._work = None
 
+    def variants(self):
+        """Bit mask of the size codes whose two-level split runs variant 1
+        (dc_batched_plan_variants), or None for plans off the fixed engine."""
+        v = ctypes.c_uint32(0)
+        if _native.lib().dc_batched_plan_variants(self.handle, ctypes.byref(v)) != 0:
+            return None
+        return v.value
+
+    def set_variants(self, mask):
+        """Rebuilds the task queue with the given split variants
+        (dc_batched_plan_set_variants)."""
+        check(_native.lib().dc_batched_plan_set_variants(self.handle, int(mask) & 0xFFFFFFFF),
+              "dc_batched_plan_set_variants")
+        ws = ctypes.c_size_t(0)
+        check(_native.lib().dc_batched_plan_workspace_size(self.handle, ctypes.byref(ws)), "workspace")
+        self.workspace_bytes = int(ws.value)
+        self._work = None
+
     def workspace(self, device):
         device = torch.device(device)
         if device.type == "cuda" and device.index is None:

@@ -49,8 +49,8 @@ struct dc_batched_plan {
   fx::Task* d_tasks = nullptr;
   fx::L2Inst* d_l2 = nullptr;
   int64_t* d_l1tmp = nullptr;
-  const void* tabs[fx::kNumSizes] = {};
-  const void* stabs[fx::kNumSizes] = {};   // stage-twiddle tables (null: none)
+  const void* tabs[fx::kNumCodes] = {};    // root tables per kernel code
+  const void* stabs[fx::kNumCodes] = {};   // stage-twiddle tables (null: none)
   size_t cnt_bytes = 0;   // header + counters, zeroed before each launch
   fx::Schedule fx_sched{0, 0};   // queue order of the fixed engine
   std::vector<int64_t> off_host;
@@ -79,16 +79,27 @@ struct FxOps {
   dc_status (*launch)(const fx::FxArgs&, int, int, cudaStream_t);
   void (*code_tabs)(int, int*, int*);
   dc_status (*stage_tables)(int, const void**);
+  bool (*code_ok)(int, int);
 };
 static const FxOps kFx32{fx::f32::size_code,      fx::f32::code_size,  fx::f32::code_shape, fx::f32::code_smem,
                          fx::f32::build_plan,     fx::f32::prepare_kernel, fx::f32::launch, fx::f32::code_tabs,
-                         fx::f32::stage_tables};
+                         fx::f32::stage_tables, fx::f32::code_ok};
 static const FxOps kFx64{fx::f64::size_code,      fx::f64::code_size,  fx::f64::code_shape, fx::f64::code_smem,
                          fx::f64::build_plan,     fx::f64::prepare_kernel, fx::f64::launch, fx::f64::code_tabs,
-                         fx::f64::stage_tables};
+                         fx::f64::stage_tables, fx::f64::code_ok};
 
 namespace {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// The largest dynamic shared memory of any kernel code of a precision: the
+// kernels' attribute is set to it everywhere, so that no caller lowers it
+// below what another plan launches with.
+int fx_smem_all(const FxOps* ops) {
+  int smem = 0;
+  for (int c = 0; c < fx::kNumCodes; ++c)
+    if (ops->code_ok(c, fx::MODE_COMPLEX)) smem = std::max(smem, ops->code_smem(c));
+  return smem;
+}
 
 double item_cost(const CfgDev& c, int count) {
   // six sub-transforms of length L per instance plus the level-2 passes
@@ -211,7 +222,32 @@ dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
   DC_CUDA_TRY(cudaMemcpy(p->d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   p->cnt_bytes = align_up(sizeof(WorkHeader) + hp.ncnt * sizeof(uint32_t), 256);
   p->work = fx_work_bytes(p);
+  p->smem = hp.smem;
   return DC_OK;
+}
+
+// root and stage-twiddle tables of every kernel code of the plan's queue
+dc_status fx_tables(dc_batched_plan* p) {
+  for (int c : p->hp.codes) {
+    if (!p->tabs[c]) {
+      dc_status st = get_root_table((fx::mode_tables_3m(p->mode) ? 3 : 2) * p->ops->code_size(c), p->ds, &p->tabs[c]);
+      if (st != DC_OK) return st;
+    }
+    if (!p->stabs[c]) {
+      dc_status st = p->ops->stage_tables(c, &p->stabs[c]);
+      if (st != DC_OK) return st;
+    }
+  }
+  return DC_OK;
+}
+
+// rebuilds the queue of plan p in schedule sc (tables, upload)
+dc_status fx_rebuild(dc_batched_plan* p, const int64_t* m, int32_t n, const std::vector<int64_t>& off,
+                     const fx::Schedule& sc) {
+  if (!p->ops->build_plan(m, n, off.data(), sc, p->mode, &p->hp)) return DC_ERR_SIZE;
+  dc_status st = fx_tables(p);
+  if (st != DC_OK) return st;
+  return fx_upload(p, off);
 }
 
 fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void* h, void* work,
@@ -237,7 +273,7 @@ fx::FxArgs fx_args(const dc_batched_plan* p, const void* f, const void* g, void*
   auto aliases = [&](const void* o) { return o && (o == f || o == g || o == e || o == e2); };
   a.in_place = (aliases(h) || aliases(h2)) ? 1 : 0;
   a.wait_limit = fx::kWaitLimit;
-  for (int c = 0; c < fx::kNumSizes; ++c) {
+  for (int c = 0; c < fx::kNumCodes; ++c) {
     a.tab[c] = p->tabs[c];
     a.stab[c] = p->stabs[c];
     if (p->stabs[c]) p->ops->code_tabs(c, &a.stab_n[c], &a.stab_off[c]);
@@ -338,41 +374,57 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
   p->off_host = off;
   int bps = 0;
   // kernel attributes for the largest shared-memory need of any size
-  int smem_all = 0;
-  for (int c = 0; c < fx::kNumSizes; ++c) smem_all = std::max(smem_all, p->ops->code_smem(c));
-  dc_status st = p->ops->prepare_kernel(smem_all, &bps);
+  dc_status st = p->ops->prepare_kernel(fx_smem_all(p->ops), &bps);
   if (st != DC_OK) return st;
   p->grid = bps * device_info().sms;
   const fx::Schedule dflt{p->grid / 2, 0};
   const bool plain = (flags & DC_PLAN_ONE_PER_LAUNCH) != 0;
   if (plain ? !fx_build_plain(p, m, n, off) : !p->ops->build_plan(m, n, off.data(), dflt, p->mode, &p->hp))
     return DC_ERR_SIZE;
-  p->smem = p->hp.smem;
-  for (int c : p->hp.codes) {
-    const void* tw = nullptr;
-    st = get_root_table((fx::mode_tables_3m(mode) ? 3 : 2) * p->ops->code_size(c), p->ds, &tw);
-    if (st != DC_OK) return st;
-    p->tabs[c] = tw;
-    st = p->ops->stage_tables(c, &p->stabs[c]);
-    if (st != DC_OK) return st;
-  }
+  st = fx_tables(p);
+  if (st != DC_OK) return st;
   st = fx_upload(p, off);
   if (st != DC_OK) return st;
   p->fx_sched = dflt;
   if ((flags & DC_PLAN_AUTOTUNE) && !plain) {
+    cudaStream_t s;
+    DC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    // The split of each two-level size (the row and column lengths, the
+    // column tile width and the threads per row follow from it): variant 0
+    // or 1, timed on the instances of that size alone, kept where it is at
+    // least 1 % faster.
+    uint32_t vmask = 0;
+    for (int c = 0; c < fx::kNumSizes; ++c) {
+      if (!p->ops->code_ok(c + fx::kCodeStride, p->mode)) continue;
+      std::vector<int64_t> mc, oc;
+      for (int32_t i = 0; i < n; ++i)
+        if (p->ops->size_code(m[i]) == c) {
+          mc.push_back(m[i]);
+          oc.push_back(off[i]);
+        }
+      if (mc.empty()) continue;
+      float tv[2] = {-1, -1};
+      for (int v = 0; v < 2; ++v) {
+        fx::Schedule sc = dflt;
+        sc.variants = (uint32_t)v << c;
+        if (fx_rebuild(p, mc.data(), (int32_t)mc.size(), oc, sc) == DC_OK) tv[v] = fx_time(p, s);
+      }
+      if (tv[0] > 0 && tv[1] > 0 && tv[1] < 0.99f * tv[0]) vmask |= 1u << c;
+    }
     // the queue order: pipeline distance between the level-2 passes (waits
     // against scratch footprint in L2), the placement of level-1 work, and
     // the tiles or row groups per pass task (hand-over against balance)
-    cudaStream_t s;
-    DC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     fx::Schedule best = dflt;
-    float tbest = fx_time(p, s);
+    best.variants = vmask;
+    float tbest = -1;
+    if (fx_rebuild(p, m, n, off, best) == DC_OK) tbest = fx_time(p, s);
     for (int cand : {p->grid / 4, p->grid / 2, p->grid}) {
       for (int mode = 0; mode < fx::kL1Modes; ++mode) {
         for (int units : {1, 2, 4}) {
-          const fx::Schedule sc{cand, mode, units};
+          fx::Schedule sc{cand, mode, units};
+          sc.variants = vmask;
           if (cand < 1 || (cand == dflt.batch_target && mode == dflt.l1_mode && units == dflt.units)) continue;
-          if (!p->ops->build_plan(m, n, off.data(), sc, p->mode, &p->hp) || fx_upload(p, off) != DC_OK) continue;
+          if (fx_rebuild(p, m, n, off, sc) != DC_OK) continue;
           const float t = fx_time(p, s);
           if (t > 0 && (tbest < 0 || t < tbest)) { tbest = t; best = sc; }
         }
@@ -380,8 +432,7 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
     }
     cudaStreamDestroy(s);
     cudaGetLastError();
-    if (!p->ops->build_plan(m, n, off.data(), best, p->mode, &p->hp)) return DC_ERR_SIZE;
-    st = fx_upload(p, off);
+    st = fx_rebuild(p, m, n, off, best);
     if (st != DC_OK) return st;
     p->fx_sched = best;
   }
@@ -553,9 +604,7 @@ dc_status dc_selftest_wait_timeout(void* work, size_t work_bytes, int64_t cycles
   if (work_bytes < need) return DC_ERR_NOMEM;
   cudaStream_t s = (cudaStream_t)stream;
   int bps = 0;
-  int smem = 0;
-  for (int c = 0; c < fx::kNumSizes; ++c) smem = std::max(smem, fx::f32::code_smem(c));
-  dc_status st = fx::f32::prepare_kernel(smem, &bps);
+  dc_status st = fx::f32::prepare_kernel(fx_smem_all(&kFx32), &bps);
   if (st != DC_OK) return st;
   static const fx::Task task{(fx::T_B << 8) | 0, 0, 0, 0, 1u, -1};
   char* w = (char*)work;
@@ -583,9 +632,9 @@ dc_status dc_batched_plan_set_schedule(dc_batched_plan* p, int32_t batch_target,
     return DC_ERR_ARG;
   std::vector<int64_t> ms(p->n);
   for (int32_t i = 0; i < p->n; ++i) ms[i] = p->off_host[i + 1] - p->off_host[i];
-  const fx::Schedule sc{batch_target, l1_mode, p->fx_sched.units};
-  if (!p->ops->build_plan(ms.data(), p->n, p->off_host.data(), sc, p->mode, &p->hp)) return DC_ERR_SIZE;
-  dc_status st = fx_upload(p, p->off_host);
+  fx::Schedule sc{batch_target, l1_mode, p->fx_sched.units};
+  sc.variants = p->fx_sched.variants;
+  dc_status st = fx_rebuild(p, ms.data(), p->n, p->off_host, sc);
   if (st != DC_OK) return st;
   p->fx_sched = sc;
   return DC_OK;
@@ -601,9 +650,30 @@ dc_status dc_batched_plan_set_task_units(dc_batched_plan* p, int32_t units) {
   if (!p || !p->fx || !p->inst_first.empty() || units < 1 || units > fx::kMaxUnits) return DC_ERR_ARG;
   std::vector<int64_t> ms(p->n);
   for (int32_t i = 0; i < p->n; ++i) ms[i] = p->off_host[i + 1] - p->off_host[i];
-  const fx::Schedule sc{p->fx_sched.batch_target, p->fx_sched.l1_mode, units};
-  if (!p->ops->build_plan(ms.data(), p->n, p->off_host.data(), sc, p->mode, &p->hp)) return DC_ERR_SIZE;
-  dc_status st = fx_upload(p, p->off_host);
+  fx::Schedule sc{p->fx_sched.batch_target, p->fx_sched.l1_mode, units};
+  sc.variants = p->fx_sched.variants;
+  dc_status st = fx_rebuild(p, ms.data(), p->n, p->off_host, sc);
+  if (st != DC_OK) return st;
+  p->fx_sched = sc;
+  return DC_OK;
+}
+
+dc_status dc_batched_plan_variants(const dc_batched_plan* p, uint32_t* mask) {
+  if (!p || !p->fx || !p->inst_first.empty() || !mask) return DC_ERR_ARG;
+  *mask = p->fx_sched.variants;
+  return DC_OK;
+}
+
+dc_status dc_batched_plan_set_variants(dc_batched_plan* p, uint32_t mask) {
+  if (!p || !p->fx || !p->inst_first.empty()) return DC_ERR_ARG;
+  std::vector<int64_t> ms(p->n);
+  for (int32_t i = 0; i < p->n; ++i) ms[i] = p->off_host[i + 1] - p->off_host[i];
+  fx::Schedule sc = p->fx_sched;
+  // only sizes that have a second split keep their bit
+  sc.variants = 0;
+  for (int c = 0; c < fx::kNumSizes; ++c)
+    if (((mask >> c) & 1u) && p->ops->code_ok(c + fx::kCodeStride, p->mode)) sc.variants |= 1u << c;
+  dc_status st = fx_rebuild(p, ms.data(), p->n, p->off_host, sc);
   if (st != DC_OK) return st;
   p->fx_sched = sc;
   return DC_OK;
@@ -808,15 +878,12 @@ size_t fx_uniform_work(int64_t n, int64_t m, int ds, int mode) {
 
 size_t fx_uniform_work_uncached(int64_t n, int64_t m, int ds, int mode) {
   const FxOps* ops = ds == 8 ? &kFx32 : &kFx64;
-  int smem_all = 0;
-  for (int c = 0; c < fx::kNumSizes; ++c) smem_all = std::max(smem_all, ops->code_smem(c));
   const int bps = ds == 8 ? 2 : 1;   // the kernel's blocks per SM (launch bounds)
   std::vector<int64_t> ms((size_t)n, m), off((size_t)n + 1, 0);
   for (int64_t i = 0; i < n; ++i) off[i + 1] = off[i] + m;
   fx::HostPlan hp;
   const fx::Schedule sc{bps * device_info().sms / 2, 0};
   if (!ops->build_plan(ms.data(), (int32_t)n, off.data(), sc, mode, &hp)) return 0;
-  (void)smem_all;
   return align_up(sizeof(WorkHeader) + hp.ncnt * sizeof(uint32_t), 256) + align_up(hp.scratch * (size_t)ds, 256) +
          hp.l1_elems * (size_t)ds;
 }

@@ -98,14 +98,17 @@ __host__ __device__ constexpr int family_E(int L) {
   return odd_part(L) == 1 ? 16 : (odd_part(L) == 3 ? 24 : 20);
 }
 __host__ __device__ constexpr bool is_level1(int m) { return m <= kThreads * family_E(m); }
-__host__ __device__ constexpr int l2_cols(int m) { return m <= 32768 ? 128 : 256; }   // L2
-__host__ __device__ constexpr int l2_rows(int m) { return m / l2_cols(m); }           // L1
+// Two-level split m = L1 L2 (L2: the column transforms' length).  Variant 0
+// takes L2 = 128 up to m = 32768 and 256 above; variant 1 the other one of
+// the two (the autotuner picks per size, FP32 binary complex plans only).
+__host__ __device__ constexpr int l2_cols(int m, int v = 0) { return (m <= 32768) != (v == 1) ? 128 : 256; }
+__host__ __device__ constexpr int l2_rows(int m, int v = 0) { return m / l2_cols(m, v); }   // L1
 // column transforms: 16 elements per thread where the tile width divides
 // the row length, else 8; tile width W = columns per block-wide tile
-__host__ __device__ constexpr int col_E(int m) {
-  return l2_rows(m) % (kThreads * 16 / l2_cols(m)) == 0 ? 16 : 8;
+__host__ __device__ constexpr int col_E(int m, int v = 0) {
+  return l2_rows(m, v) % (kThreads * 16 / l2_cols(m, v)) == 0 ? 16 : 8;
 }
-__host__ __device__ constexpr int col_width(int m) { return kThreads * col_E(m) / l2_cols(m); }
+__host__ __device__ constexpr int col_width(int m, int v = 0) { return kThreads * col_E(m, v) / l2_cols(m, v); }
 __host__ __device__ constexpr int padded(int L) { return (L + (L >> 4) + 2) & ~1; }
 // Element stride between the array pairs (A, B) of consecutive thread groups
 // of T threads.  When several groups share a half-warp (T < 16) the stride

@@ -14,6 +14,11 @@ namespace dc {
 namespace fx {
 
 constexpr int kNumSizes = 31;   // {2^a, 3*2^a, 5*2^a} in [64, 65536]
+// A kernel code names a size and a variant of its two-level split:
+// code = size code + kCodeStride * variant (variant 1: FP32 binary complex
+// plans, two-level sizes only).
+constexpr int kCodeStride = 32;
+constexpr int kNumCodes = 2 * kCodeStride;
 
 // task types of the persistent queue
 enum : int32_t { T_L1 = 0, T_A = 1, T_B = 2, T_C = 3 };
@@ -76,12 +81,12 @@ struct FxArgs {
   int32_t in_place;        // an output is an input
   int32_t mode;            // MODE_*
   long long wait_limit;    // SM cycles a dependency wait may take before DC_ERR_TIMEOUT
-  const void* tab[kNumSizes];     // root tables zeta_{2m}^i, i < 2m, per size code
-  // stage-twiddle tables per size code (null for sizes without): stab_n
+  const void* tab[kNumCodes];     // root tables zeta_{2m}^i, i < 2m, per kernel code
+  // stage-twiddle tables per kernel code (null for sizes without): stab_n
   // entries, copied to byte stab_off of the block's shared memory
-  const void* stab[kNumSizes];
-  int32_t stab_n[kNumSizes];
-  int32_t stab_off[kNumSizes];
+  const void* stab[kNumCodes];
+  int32_t stab_n[kNumCodes];
+  int32_t stab_off[kNumCodes];
 };
 
 struct HostPlan {
@@ -102,10 +107,13 @@ struct HostPlan {
 // pipeline, 1 the larger half spread over the pipeline and the rest after
 // it, 2 before it.  units: column tiles or row groups per pass task (1, 2
 // or 4): fewer, longer tasks spend less of the launch handing over.
+// variants: bit c set runs the two-level size of size code c in variant 1
+// of its split (honoured for FP32 binary complex plans).
 struct Schedule {
   int batch_target;
   int l1_mode;
   int units = 1;
+  uint32_t variants = 0;
 };
 constexpr int kMaxUnits = 4;
 constexpr int kL1Modes = 3;
@@ -115,6 +123,8 @@ constexpr long long kWaitLimit = 1ll << 32;   // about two seconds at 2 GHz
 #define DC_FX_DECLARE                                                                       \
   /* size code of m, or -1 when m is not in the set */                                      \
   int size_code(int64_t m);                                                                 \
+  /* whether kernel code `code` (size code + kCodeStride * variant) exists for a kind */    \
+  bool code_ok(int code, int mode);                                                         \
   int64_t code_size(int code);                                                              \
   /* instances per task (level 1) or the level-2 split of a size code */                    \
   void code_shape(int code, int* level, int* per_task, int* L1, int* L2, int* W);           \

@@ -68,17 +68,24 @@ __host__ __device__ constexpr int roots_count(int TN) {
 }
 
 constexpr int kBlocksPerSM = kDouble ? 1 : 2;
+// kinds whose kernel carries variant 1 of the two-level splits: FP32 binary
+// complex (the batched workload); the others run variant 0 only
+__host__ __device__ constexpr bool kVariantKind(int mode) { return !kDouble && mode == MODE_COMPLEX; }
+// size codes of the two-level sizes (8192 .. 65536, 12288 .. 49152, 10240 .. 40960)
+__host__ __device__ constexpr bool two_level_code(int c) { return (c >= 7 && c <= 10) || (c >= 18 && c <= 20) || c >= 28; }
 
-template <int M> struct Shape {
+// Shape of size M in variant V (the two-level split, fixed.cuh; one-level
+// sizes have variant 0 only)
+template <int M, int V = 0> struct Shape {
   static constexpr bool l1 = is_level1(M);
   // level 1
   static constexpr int E = family_E(M);
   static constexpr int T = M / E;
   static constexpr int G = l1 ? kThreads / T : 0;
   // level 2 (placeholders for level-1 sizes)
-  static constexpr int L2 = l1 ? 128 : l2_cols(M);
+  static constexpr int L2 = l1 ? 128 : l2_cols(M, V);
   static constexpr int L1 = l1 ? 128 : M / L2;
-  static constexpr int W = col_width(l1 ? 16384 : M);
+  static constexpr int W = l1 ? col_width(16384) : col_width(M, V);
   // rows: E = 12 for the 3 * 2^a family (24 elements per thread spill in
   // the row pass), else the family's E
   static constexpr int E1 = odd_part(L1) == 3 ? 12 : family_E(L1);
@@ -87,7 +94,7 @@ template <int M> struct Shape {
   static constexpr int nA = L1 / W;
   static constexpr int nB = 2 * L2 / GR;
   static constexpr int nBh = 3 * L2 / GR;   // centered Hermitian: three residues, one packed row each
-  static constexpr int EC = l1 ? 16 : col_E(M);
+  static constexpr int EC = l1 ? 16 : col_E(M, V);
   static_assert(l1 || (L1 % W == 0 && (2 * L2) % GR == 0 && (3 * L2) % GR == 0 && L1 * L2 == M),
                 "level-2 tiling must be exact");
   static_assert(!l1 || kThreads % T == 0, "level-1 groups must tile the block");
@@ -131,14 +138,14 @@ template <int M> struct Shape {
 // at a fixed place of the block's dynamic shared memory (so their address
 // is a constant, not a register held across the task).
 extern __shared__ __align__(16) unsigned char fx_smem[];
-template <int M> __device__ __forceinline__ TabRoots row_roots(const Roots<C>& r) {
-  return TabRoots{r, (const C*)(fx_smem + Shape<M>::tab_off)};
+template <int M, int V> __device__ __forceinline__ TabRoots row_roots(const Roots<C>& r) {
+  return TabRoots{r, (const C*)(fx_smem + Shape<M, V>::tab_off)};
 }
-template <int M> __device__ __forceinline__ TabRoots col_roots(const Roots<C>& r) {
-  return TabRoots{r, (const C*)(fx_smem + Shape<M>::tab_off) + Shape<M>::tab_col};
+template <int M, int V> __device__ __forceinline__ TabRoots col_roots(const Roots<C>& r) {
+  return TabRoots{r, (const C*)(fx_smem + Shape<M, V>::tab_off) + Shape<M, V>::tab_col};
 }
-template <int M> __device__ __forceinline__ void gen_size_tabs(C* st) {
-  using S = Shape<M>;
+template <int M, int V> __device__ __forceinline__ void gen_size_tabs(C* st) {
+  using S = Shape<M, V>;
   if constexpr (!S::l1) {
     gen_stage_tabs<S::L1, S::E1>(st);
     if constexpr (!S::tab_same) gen_stage_tabs<S::L2, S::EC>(st + S::tab_col);
@@ -405,9 +412,9 @@ __device__ __noinline__ void l1_hdot2_residue(const FxArgs* a, int ri, int first
 
 // pass A: column tile `tile` of level-2 instance l.  Each pass is its own
 // function so that registers are allocated per pass.
-template <int M>
+template <int M, int V>
 __device__ __noinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
-  using S = Shape<M>;
+  using S = Shape<M, V>;
   constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 2 * M;
   using K = Stage<L2, E, 0, false>;
   const int c = threadIdx.x % W, i = threadIdx.x / W;
@@ -458,7 +465,7 @@ __device__ __noinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, Root
       for (int e = 0; e < E; ++e) v[e] = r ? cmul(raw[e], tw[e]) : raw[e];
       // S[j2][k1]; the factor zeta_m^{j2 k1} is applied in pass B
       C* dst = scr + (size_t)(2 * r + arr) * M + k1;
-      column<L2, E, W, TN, false>(v, i, sm + c, col_roots<M>(rt), [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
+      column<L2, E, W, TN, false>(v, i, sm + c, col_roots<M, V>(rt), [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
       __syncthreads();
     }
   }
@@ -471,9 +478,9 @@ __device__ __noinline__ void run_A(const FxArgs* a, int l, int tile, C* sm, Root
 // (second).  With B_k = U_k (k < m), conj U_{2m-k} (k > m), V_k equals
 // zeta_{4m}^{rk} B_k times (-1)^r above m, since zeta_{4m}^{2m} = -1; the
 // residue-1 factor below carries that sign.
-template <int M>
+template <int M, int V>
 __device__ __noinline__ void run_A_tern(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
-  using S = Shape<M>;
+  using S = Shape<M, V>;
   constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 2 * M, MH = M / 2;
   using K = Stage<L2, E, 0, false>;
   const int c = threadIdx.x % W, i = threadIdx.x / W;
@@ -535,7 +542,7 @@ __device__ __noinline__ void run_A_tern(const FxArgs* a, int l, int tile, C* sm,
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = r ? cmul(raw[e], tw[e]) : raw[e];
       C* dst = scr + (size_t)(2 * r + arr) * M + k1;
-      column<L2, E, W, TN, false>(v, i, sm + c, col_roots<M>(rt), [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
+      column<L2, E, W, TN, false>(v, i, sm + c, col_roots<M, V>(rt), [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
       __syncthreads();
     }
   }
@@ -554,9 +561,9 @@ struct TernProd {
 
 // pass B: row group `unit` (rows (r, j2), r = row / L2) of level-2 instance
 // l; TERN: the ternary product of a ternary convolution's sub-transforms
-template <int M, bool TERN>
+template <int M, int V, bool TERN>
 __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Roots<C> rt) {
-  using S = Shape<M>;
+  using S = Shape<M, V>;
   constexpr int L1 = S::L1, L2 = S::L2, E1 = S::E1, T1 = S::T1, GR = S::GR, PL = padded(L1),
                 GS = group_stride(L1, T1), TN = 2 * M;
   const int gi = threadIdx.x / T1, i = threadIdx.x % T1;
@@ -573,7 +580,7 @@ __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Root
   static_assert(E1 <= 20, "rows hold their twiddles in registers");
   C tw[E1];
   conv_residue<L1, E1, TN>(
-      i, true, A, B, row_roots<M>(rt),
+      i, true, A, B, row_roots<M, V>(rt),
       [&](int x, int arr, int e) {
         if (arr == 0) tw[e] = rt.at(2 * j2 * x);
         return cmul(__ldcg((arr ? sg : (const C*)sf) + x), tw[e]);
@@ -587,9 +594,9 @@ __device__ __noinline__ void run_B(const FxArgs* a, int l, int unit, C* sm, Root
 
 // pass C: column tile `tile` of level-2 instance l, both residues, output;
 // TERN: only the outputs k < M / 2 (a ternary convolution's length)
-template <int M, bool TERN>
+template <int M, int V, bool TERN>
 __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
-  using S = Shape<M>;
+  using S = Shape<M, V>;
   constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 2 * M;
   using K = Stage<L2, E, 0, true>;
   const int c = threadIdx.x % W, i = threadIdx.x / W;
@@ -608,9 +615,9 @@ __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Root
 #pragma unroll
       for (int q = 0; q < K::R; ++q) vin[r][b * K::R + q] = __ldcg(src + (size_t)L1 * pos<L2, E, 0, true>(i, b, q));
   }
-  column<L2, E, W, TN, true>(vin[0], i, sm + c, col_roots<M>(rt), [&](int, int e, C y) { y0[e] = y; });
+  column<L2, E, W, TN, true>(vin[0], i, sm + c, col_roots<M, V>(rt), [&](int, int e, C y) { y0[e] = y; });
   __syncthreads();
-  column<L2, E, W, TN, true>(vin[1], i, sm + c, col_roots<M>(rt), [&](int k2, int e, C y) {
+  column<L2, E, W, TN, true>(vin[1], i, sm + c, col_roots<M, V>(rt), [&](int k2, int e, C y) {
     const int k = k1 + L1 * k2;
     if (!TERN || 2 * k2 < L2) h[(size_t)L1 * k2] = cscale(cadd(y0[e], cmulc(y, rt.at(k))), sc);
   });
@@ -632,9 +639,9 @@ __device__ __noinline__ void run_C(const FxArgs* a, int l, int tile, C* sm, Root
 // and Q_k = conj f_{m-k} + i conj g_{m-k}, residue r's packed input is
 // zeta_{3m}^{rk} (P_k + zeta_3^{-r} Q_k) (Eqs. (2.4)-(2.5) with Hermitian
 // symmetry); at k = 0 it is Re f_0 + i Re g_0 for every r.
-template <int M>
+template <int M, int V>
 __device__ __noinline__ void run_A_herm(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
-  using S = Shape<M>;
+  using S = Shape<M, V>;
   constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 3 * M;
   using K = Stage<L2, E, 0, false>;
   const int c = threadIdx.x % W, i = threadIdx.x / W;
@@ -678,7 +685,7 @@ __device__ __noinline__ void run_A_herm(const FxArgs* a, int l, int tile, C* sm,
       }
     // S_r[j2][k1]; the factor zeta_m^{j2 k1} is applied in pass B
     C* dst = scr + (size_t)ri * M + k1;
-    column<L2, E, W, TN, false>(v, i, sm + c, col_roots<M>(rt), [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
+    column<L2, E, W, TN, false>(v, i, sm + c, col_roots<M, V>(rt), [&](int j2, int, C y) { __stcg(dst + (size_t)j2 * L1, y); });
     __syncthreads();
   }
 }
@@ -686,9 +693,9 @@ __device__ __noinline__ void run_A_herm(const FxArgs* a, int l, int tile, C* sm,
 // pass B: row group `unit` (rows (ri, j2), ri = row / L2) of level-2
 // instance l: times zeta_m^{j2 k1}, backward row transform, the real
 // product u^f u^g, forward row transform, times zeta_m^{-j2 k1}, in place
-template <int M>
+template <int M, int V>
 __device__ __noinline__ void run_B_herm(const FxArgs* a, int l, int unit, C* sm, Roots<C> rt) {
-  using S = Shape<M>;
+  using S = Shape<M, V>;
   constexpr int L1 = S::L1, L2 = S::L2, E1 = S::E1, T1 = S::T1, GR = S::GR, GS = group_stride(L1, T1),
                 TN = 3 * M;
   const int gi = threadIdx.x / T1, i = threadIdx.x % T1;
@@ -699,7 +706,7 @@ __device__ __noinline__ void run_B_herm(const FxArgs* a, int l, int unit, C* sm,
   static_assert(E1 <= 20, "rows hold their twiddles in registers");
   C tw[E1];
   conv1_residue<L1, E1, TN>(
-      i, sm + gi * GS, row_roots<M>(rt),
+      i, sm + gi * GS, row_roots<M, V>(rt),
       [&](int x, int e) {
         tw[e] = rt.at(3 * j2 * x);
         return cmul(__ldcg(s + x), tw[e]);
@@ -710,9 +717,9 @@ __device__ __noinline__ void run_B_herm(const FxArgs* a, int l, int unit, C* sm,
 // pass C: column tile `tile` of level-2 instance l: the forward column
 // transforms of the three residues, recombined as
 // h_k = sum_r zeta_{3m}^{-rk} S_r(k) / 3m (Eq. (2.7)), k < m
-template <int M>
+template <int M, int V>
 __device__ __noinline__ void run_C_herm(const FxArgs* a, int l, int tile, C* sm, Roots<C> rt) {
-  using S = Shape<M>;
+  using S = Shape<M, V>;
   constexpr int L1 = S::L1, L2 = S::L2, W = S::W, E = S::EC, TN = 3 * M;
   using K = Stage<L2, E, 0, true>;
   const int c = threadIdx.x % W, i = threadIdx.x / W;
@@ -731,7 +738,7 @@ __device__ __noinline__ void run_C_herm(const FxArgs* a, int l, int tile, C* sm,
     for (int b = 0; b < K::NB; ++b)
 #pragma unroll
       for (int q = 0; q < K::R; ++q) v[b * K::R + q] = __ldcg(src + (size_t)L1 * pos<L2, E, 0, true>(i, b, q));
-    column<L2, E, W, TN, true>(v, i, sm + c, col_roots<M>(rt), [&](int k2, int e, C y) {
+    column<L2, E, W, TN, true>(v, i, sm + c, col_roots<M, V>(rt), [&](int k2, int e, C y) {
       if (r != 0) {
         const C t = rt.at(k1 + L1 * k2);
         y = r > 0 ? cmulc(y, t) : cmul(y, t);
@@ -755,7 +762,7 @@ __device__ __noinline__ void run_C_herm(const FxArgs* a, int l, int tile, C* sm,
 // graph (and the registers ptxas gives its functions) holds only its own
 // passes.
 
-template <int M, int MODE>
+template <int M, int V, int MODE>
 __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, int units, C* sm, Roots<C> rt) {
   if constexpr (Shape<M>::l1) {
     if constexpr (MODE == MODE_HERM) {
@@ -796,17 +803,17 @@ __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, i
       for (int u = 0; u < units; ++u) {
         if (u) __syncthreads();
         if constexpr (MODE == MODE_HERM) {
-          if (type == T_A) run_A_herm<M>(a, x, y + u, sm, rt);
-          else if (type == T_B) run_B_herm<M>(a, x, y + u, sm, rt);
-          else run_C_herm<M>(a, x, y + u, sm, rt);
+          if (type == T_A) run_A_herm<M, V>(a, x, y + u, sm, rt);
+          else if (type == T_B) run_B_herm<M, V>(a, x, y + u, sm, rt);
+          else run_C_herm<M, V>(a, x, y + u, sm, rt);
         } else if constexpr (MODE == MODE_TERN) {
-          if (type == T_A) run_A_tern<M>(a, x, y + u, sm, rt);
-          else if (type == T_B) run_B<M, true>(a, x, y + u, sm, rt);
-          else run_C<M, true>(a, x, y + u, sm, rt);
+          if (type == T_A) run_A_tern<M, V>(a, x, y + u, sm, rt);
+          else if (type == T_B) run_B<M, V, true>(a, x, y + u, sm, rt);
+          else run_C<M, V, true>(a, x, y + u, sm, rt);
         } else {
-          if (type == T_A) run_A<M>(a, x, y + u, sm, rt);
-          else if (type == T_B) run_B<M, false>(a, x, y + u, sm, rt);
-          else run_C<M, false>(a, x, y + u, sm, rt);
+          if (type == T_A) run_A<M, V>(a, x, y + u, sm, rt);
+          else if (type == T_B) run_B<M, V, false>(a, x, y + u, sm, rt);
+          else run_C<M, V, false>(a, x, y + u, sm, rt);
         }
       }
     }
@@ -887,12 +894,12 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
     const long long t_got = clock64();
     if (code != cur) {
       // lo = zeta_TN^b (b < 2^sh), hi = zeta_TN^(a 2^sh), from the full table
-      const int TN = (mode_tables_3m(MODE) ? 3 : 2) * size_of_code(code);
+      const int TN = (mode_tables_3m(MODE) ? 3 : 2) * size_of_code(code % kCodeStride);
       const int sh = roots_sh(TN), nlo = 1 << sh, cnt = roots_count(TN);
       const C* tab = (const C*)a.tab[code];
       // the low table always starts shared memory; the high one follows it,
       // or sits behind the task data for the Hermitian level-2 sizes
-      const int hoff = roots_off_of(code, mode_tables_3m(MODE));
+      const int hoff = roots_off_of(code % kCodeStride, mode_tables_3m(MODE));
       C* hi = hoff ? (C*)(smem_raw + hoff) : rts + nlo;
       // and the size's stage tables (a contiguous copy) behind its task data
       const C* stab = (const C*)a.stab[code];
@@ -910,17 +917,29 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
       atomicAdd(&a.hdr->handover_cycles, (unsigned long long)(t_got - t_end));
       atomicAdd(&a.hdr->table_cycles, (unsigned long long)(t_start - t_got));
     }
-    switch (code) {
+    if (code < kCodeStride) {
+      switch (code) {
 #define DC_FX_CASE(c) \
-      case c: run_size<size_of_code(c), MODE>(&a, type, t.a, t.b, units, sm, rt); break;
-      DC_FX_CASE(0) DC_FX_CASE(1) DC_FX_CASE(2) DC_FX_CASE(3) DC_FX_CASE(4) DC_FX_CASE(5)
-      DC_FX_CASE(6) DC_FX_CASE(7) DC_FX_CASE(8) DC_FX_CASE(9) DC_FX_CASE(10)
-      DC_FX_CASE(11) DC_FX_CASE(12) DC_FX_CASE(13) DC_FX_CASE(14) DC_FX_CASE(15)
-      DC_FX_CASE(16) DC_FX_CASE(17) DC_FX_CASE(18) DC_FX_CASE(19) DC_FX_CASE(20)
-      DC_FX_CASE(21) DC_FX_CASE(22) DC_FX_CASE(23) DC_FX_CASE(24) DC_FX_CASE(25)
-      DC_FX_CASE(26) DC_FX_CASE(27) DC_FX_CASE(28) DC_FX_CASE(29) DC_FX_CASE(30)
+        case c: run_size<size_of_code(c), 0, MODE>(&a, type, t.a, t.b, units, sm, rt); break;
+        DC_FX_CASE(0) DC_FX_CASE(1) DC_FX_CASE(2) DC_FX_CASE(3) DC_FX_CASE(4) DC_FX_CASE(5)
+        DC_FX_CASE(6) DC_FX_CASE(7) DC_FX_CASE(8) DC_FX_CASE(9) DC_FX_CASE(10)
+        DC_FX_CASE(11) DC_FX_CASE(12) DC_FX_CASE(13) DC_FX_CASE(14) DC_FX_CASE(15)
+        DC_FX_CASE(16) DC_FX_CASE(17) DC_FX_CASE(18) DC_FX_CASE(19) DC_FX_CASE(20)
+        DC_FX_CASE(21) DC_FX_CASE(22) DC_FX_CASE(23) DC_FX_CASE(24) DC_FX_CASE(25)
+        DC_FX_CASE(26) DC_FX_CASE(27) DC_FX_CASE(28) DC_FX_CASE(29) DC_FX_CASE(30)
 #undef DC_FX_CASE
-      default: break;
+        default: break;
+      }
+    } else if constexpr (kVariantKind(MODE)) {
+      // variant 1 of the two-level sizes (the other split)
+      switch (code - kCodeStride) {
+#define DC_FX_CASE1(c) \
+        case c: run_size<size_of_code(c), 1, MODE>(&a, type, t.a, t.b, units, sm, rt); break;
+        DC_FX_CASE1(7) DC_FX_CASE1(8) DC_FX_CASE1(9) DC_FX_CASE1(10) DC_FX_CASE1(18) DC_FX_CASE1(19)
+        DC_FX_CASE1(20) DC_FX_CASE1(28) DC_FX_CASE1(29) DC_FX_CASE1(30)
+#undef DC_FX_CASE1
+        default: break;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -970,37 +989,37 @@ dc_status DC_FX_CAT(launch_mode, DC_FX_MODE)(const FxArgs& a, int grid, int smem
 #undef DC_FX_CAT2
 #else
 namespace {
-template <int... Cs> struct CodeTable {
-  static void fill(int* lvl, int* per, int* l1, int* l2, int* w, int* na, int* nb, int* nbh, int* smem) {
-    int k = 0;
-    ((lvl[k] = Shape<size_of_code(Cs)>::l1 ? 1 : 2, per[k] = Shape<size_of_code(Cs)>::G,
-      l1[k] = Shape<size_of_code(Cs)>::L1, l2[k] = Shape<size_of_code(Cs)>::L2, w[k] = Shape<size_of_code(Cs)>::W,
-      na[k] = Shape<size_of_code(Cs)>::nA, nb[k] = Shape<size_of_code(Cs)>::nB,
-      nbh[k] = Shape<size_of_code(Cs)>::nBh,
-      smem[k] = Shape<size_of_code(Cs)>::total, ++k), ...);
+template <int V, int... Cs> struct CodeTable {
+  static void fill(int* lvl, int* per, int* l1, int* l2, int* w, int* na, int* nb, int* nbh, int* smem, int* tabn,
+                   int* taboff) {
+    int k = V * kCodeStride;
+    ((lvl[k] = Shape<size_of_code(Cs), V>::l1 ? 1 : 2, per[k] = Shape<size_of_code(Cs), V>::G,
+      l1[k] = Shape<size_of_code(Cs), V>::L1, l2[k] = Shape<size_of_code(Cs), V>::L2,
+      w[k] = Shape<size_of_code(Cs), V>::W, na[k] = Shape<size_of_code(Cs), V>::nA,
+      nb[k] = Shape<size_of_code(Cs), V>::nB, nbh[k] = Shape<size_of_code(Cs), V>::nBh,
+      smem[k] = Shape<size_of_code(Cs), V>::total, tabn[k] = Shape<size_of_code(Cs), V>::tab_entries,
+      taboff[k] = Shape<size_of_code(Cs), V>::tab_off, ++k),
+     ...);
   }
 };
-template <int... Cs> struct TabTable {
-  static void fill(int* n, int* off) {
-    int k = 0;
-    ((n[k] = Shape<size_of_code(Cs)>::tab_entries, off[k] = Shape<size_of_code(Cs)>::tab_off, ++k), ...);
-  }
-};
+// per kernel code (size code + kCodeStride * variant); variant 1 entries of
+// sizes without one repeat variant 0 and are never used
 struct Tables {
-  int lvl[kNumSizes], per[kNumSizes], l1[kNumSizes], l2[kNumSizes], w[kNumSizes], na[kNumSizes],
-      nb[kNumSizes], nbh[kNumSizes], smem[kNumSizes], tabn[kNumSizes], taboff[kNumSizes];
+  int lvl[kNumCodes], per[kNumCodes], l1[kNumCodes], l2[kNumCodes], w[kNumCodes], na[kNumCodes],
+      nb[kNumCodes], nbh[kNumCodes], smem[kNumCodes], tabn[kNumCodes], taboff[kNumCodes];
   Tables() {
-    CodeTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
-              26, 27, 28, 29, 30>::fill(lvl, per, l1, l2, w, na, nb, nbh, smem);
-    TabTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26,
-             27, 28, 29, 30>::fill(tabn, taboff);
+    std::memset(this, 0, sizeof(*this));
+    CodeTable<0, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
+              26, 27, 28, 29, 30>::fill(lvl, per, l1, l2, w, na, nb, nbh, smem, tabn, taboff);
+    CodeTable<1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25,
+              26, 27, 28, 29, 30>::fill(lvl, per, l1, l2, w, na, nb, nbh, smem, tabn, taboff);
   }
 };
 
-// the stage tables of a size, one block
-template <int M> __global__ void gen_tabs_kernel(C* st) { gen_size_tabs<M>(st); }
+// the stage tables of a kernel code, one block
+template <int M, int V> __global__ void gen_tabs_kernel(C* st) { gen_size_tabs<M, V>(st); }
 std::mutex g_tab_mu;
-std::map<std::pair<int, int>, void*> g_stage_tabs;   // (device, size code) -> tables
+std::map<std::pair<int, int>, void*> g_stage_tabs;   // (device, kernel code) -> tables
 const Tables& tables() {
   static Tables t;
   return t;
@@ -1012,8 +1031,12 @@ int size_code(int64_t m) {
     if (size_of_code(c) == m) return c;
   return -1;
 }
-int64_t code_size(int code) { return size_of_code(code); }
+int64_t code_size(int code) { return size_of_code(code % kCodeStride); }
 bool code_level1(int code) { return tables().lvl[code] == 1; }
+bool code_ok(int code, int mode) {
+  if (code < 0 || code >= kNumCodes || code % kCodeStride >= kNumSizes) return false;
+  return code < kCodeStride || (kVariantKind(mode) && two_level_code(code - kCodeStride));
+}
 int code_smem(int code) { return tables().smem[code]; }
 void code_tabs(int code, int* entries, int* byte_off) {
   *entries = tables().tabn[code];
@@ -1042,13 +1065,11 @@ dc_status stage_tables(int code, const void** out) {
     return DC_ERR_CUDA;
   }
   switch (code) {
-#define DC_FX_GEN(c) \
-    case c: gen_tabs_kernel<size_of_code(c)><<<1, kThreads, 0, s>>>((C*)p); break;
-    DC_FX_GEN(0) DC_FX_GEN(1) DC_FX_GEN(2) DC_FX_GEN(3) DC_FX_GEN(4) DC_FX_GEN(5) DC_FX_GEN(6) DC_FX_GEN(7)
-    DC_FX_GEN(8) DC_FX_GEN(9) DC_FX_GEN(10) DC_FX_GEN(11) DC_FX_GEN(12) DC_FX_GEN(13) DC_FX_GEN(14)
-    DC_FX_GEN(15) DC_FX_GEN(16) DC_FX_GEN(17) DC_FX_GEN(18) DC_FX_GEN(19) DC_FX_GEN(20) DC_FX_GEN(21)
-    DC_FX_GEN(22) DC_FX_GEN(23) DC_FX_GEN(24) DC_FX_GEN(25) DC_FX_GEN(26) DC_FX_GEN(27) DC_FX_GEN(28)
-    DC_FX_GEN(29) DC_FX_GEN(30)
+#define DC_FX_GEN(c)                                                                   \
+    case c: gen_tabs_kernel<size_of_code(c), 0><<<1, kThreads, 0, s>>>((C*)p); break;  \
+    case c + kCodeStride: gen_tabs_kernel<size_of_code(c), 1><<<1, kThreads, 0, s>>>((C*)p); break;
+    DC_FX_GEN(7) DC_FX_GEN(8) DC_FX_GEN(9) DC_FX_GEN(10) DC_FX_GEN(18) DC_FX_GEN(19) DC_FX_GEN(20)
+    DC_FX_GEN(28) DC_FX_GEN(29) DC_FX_GEN(30)
 #undef DC_FX_GEN
     default: break;
   }
@@ -1080,13 +1101,15 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   P = HostPlan{};
   std::map<int, std::vector<int32_t>> l1_by_code;
   std::vector<std::pair<int, int32_t>> big;   // (code, instance)
-  std::vector<bool> used(kNumSizes, false);
+  std::vector<bool> used(kNumCodes, false);
   P.l1tmp.assign((size_t)n, 0);
   for (int32_t i = 0; i < n; ++i) {
-    const int c = size_code(m[i]);
+    int c = size_code(m[i]);
     if (c < 0) return false;
     if ((mode == MODE_TERN && tb.lvl[c] == 1) || ((mode == MODE_PAIR || mode == MODE_HDOT2) && tb.lvl[c] == 2))
       return false;
+    // the kernel code: variant 1 of the split where the schedule asks for it
+    if (((sc.variants >> c) & 1u) && code_ok(c + kCodeStride, mode)) c += kCodeStride;
     used[c] = true;
     if (tb.lvl[c] == 1) {
       l1_by_code[c].push_back(i);
@@ -1097,7 +1120,7 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
       big.push_back({c, i});
     }
   }
-  for (int c = 0; c < kNumSizes; ++c)
+  for (int c = 0; c < kNumCodes; ++c)
     if (used[c]) {
       P.codes.push_back(c);
       P.smem = std::max(P.smem, code_smem(c));
@@ -1108,7 +1131,7 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   std::vector<L1T> l1t;
   for (auto& kv : l1_by_code) {
     const int c = kv.first, per = tb.per[c];
-    const double ms = (double)size_of_code(c);
+    const double ms = (double)size_of_code(c % kCodeStride);
     for (size_t s = 0; s < kv.second.size(); s += per) {
       L1T t;
       t.code = c;
@@ -1121,8 +1144,8 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   // the same time then run the same code (one size's code is tens of KB of
   // straight-line instructions) and refill their root tables less often
   std::stable_sort(l1t.begin(), l1t.end(), [](const L1T& x, const L1T& y) {
-    return size_of_code(x.code) != size_of_code(y.code) ? size_of_code(x.code) > size_of_code(y.code)
-                                                        : x.cost > y.cost;
+    const int mx = size_of_code(x.code % kCodeStride), my = size_of_code(y.code % kCodeStride);
+    return mx != my ? mx > my : x.cost > y.cost;
   });
   std::vector<Task> l1tasks;
   for (auto& t : l1t) {
@@ -1133,7 +1156,7 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
 
   // level-2 instances, largest first, in batches of about batch_target column tiles
   std::stable_sort(big.begin(), big.end(), [](const std::pair<int, int32_t>& x, const std::pair<int, int32_t>& y) {
-    return size_of_code(x.first) > size_of_code(y.first);
+    return size_of_code(x.first % kCodeStride) > size_of_code(y.first % kCodeStride);
   });
   const int n2 = (int)big.size();
   std::vector<std::vector<int>> batches;
@@ -1154,7 +1177,7 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   int64_t region = 0;
   for (int k = 0; k < nbat; ++k) {
     int64_t s = 0;
-    for (int l : batches[k]) s += 4 * (int64_t)size_of_code(big[l].first);
+    for (int l : batches[k]) s += 4 * (int64_t)size_of_code(big[l].first % kCodeStride);
     region = std::max(region, s);
   }
   P.l2.resize(n2);
@@ -1165,7 +1188,7 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
       const int c = big[l].first;
       P.l2[l].off = off[big[l].second];
       P.l2[l].scr = o;
-      o += 4 * (int64_t)size_of_code(c);
+      o += 4 * (int64_t)size_of_code(c % kCodeStride);
       batch_c[k] += (uint32_t)tb.na[c];
     }
   }

@@ -307,3 +307,87 @@ def test_graph_replay_matches_eager_and_oracle(dc):
     graph.replay()
     torch.cuda.synchronize()
     check_all(sizes, f2, g2, off, out.cpu().numpy())
+
+
+TWO_LEVEL = [8192, 16384, 32768, 65536, 12288, 24576, 49152, 10240, 20480, 40960]
+
+
+def size_code_of(m):
+    # the engine's size codes: 64 << c (c < 11), 96 << (c - 11), 80 << (c - 21)
+    for c, base in ((0, 64), (11, 96), (21, 80)):
+        k = m // base
+        if m % base == 0 and k & (k - 1) == 0:
+            return c + k.bit_length() - 1
+    raise ValueError(m)
+
+
+def test_split_variants_every_two_level_size(dc):
+    # variant 1 of the two-level split (L2 = 256 up to m = 32768, 128
+    # above): every two-level size, several instances each, against the
+    # oracle; describe reports the swapped split and the mask reads back
+    sizes = [m for m in TWO_LEVEL for _ in range(3)] + [640] * 20 + [64] * 70
+    rng = np.random.default_rng(41)
+    sizes = [sizes[i] for i in rng.permutation(len(sizes))]
+    f, g, off = synthetic.batched_inputs(sizes, 41)
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex64)
+    assert plan.variants() == 0
+    before = {d[0]: d for d in plan.describe()}
+    full = sum(1 << size_code_of(m) for m in TWO_LEVEL)
+    plan.set_variants(0xFFFFFFFF)
+    assert plan.variants() == full
+    after = {d[0]: d for d in plan.describe()}
+    for m in TWO_LEVEL:
+        l1, l2 = before[m][3], before[m][4]
+        assert l1 * l2 == m and after[m][3] * after[m][4] == m
+        assert after[m][4] == (256 if l2 == 128 else 128), (m, before[m], after[m])
+    assert after[640] == before[640] and after[64] == before[64]
+    tf = torch.tensor(f, dtype=torch.complex64, device="cuda")
+    tg = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    work = plan.workspace(tf.device)
+    h = plan(tf, tg, work=work)
+    torch.cuda.synchronize()
+    assert dc.read_status(work) == (0, 0)
+    check_all(sizes, f, g, off, h.cpu().numpy())
+
+
+def test_split_variant_masks_and_schedules(dc):
+    # alternating masks, with the pipeline settings: every combination gives
+    # a correct result, and the level-1 work is untouched by the mask
+    sizes = [65536] * 3 + [10240] * 5 + [24576] * 4 + [8192] * 6 + [1280] * 12 + [96] * 40
+    f, g, off = synthetic.batched_inputs(sizes, 42)
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex64)
+    tf = torch.tensor(f, dtype=torch.complex64, device="cuda")
+    tg = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    codes = [size_code_of(m) for m in (65536, 10240, 24576, 8192)]
+    for mask in ((1 << codes[0]) | (1 << codes[2]), (1 << codes[1]) | (1 << codes[3]), sum(1 << c for c in codes)):
+        for target, mode, units in ((1, 0, 1), (152, 1, 2), (38, 2, 4)):
+            plan.set_variants(mask)
+            plan.set_task_units(units)
+            plan.set_schedule(target, mode)
+            assert plan.variants() == mask
+            work = plan.workspace(tf.device)
+            h = plan(tf, tg, work=work)
+            torch.cuda.synchronize()
+            assert dc.read_status(work) == (0, 0)
+            check_all(sizes, f, g, off, h.cpu().numpy())
+
+
+def test_split_variants_fp64_ignored(dc):
+    # FP64 plans run variant 0 only: the mask is accepted and dropped
+    sizes = [16384] * 2 + [640] * 4
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex128)
+    plan.set_variants(0xFFFFFFFF)
+    assert plan.variants() == 0
+    _, f, g, off, h = run_plan(dc, sizes, 43, dtype=torch.complex128)
+    check_all(sizes, f, g, off, h, torch.complex128)
+
+
+def test_autotuned_variants_valid(dc):
+    # the autotuner's choice is a subset of the sizes that have a second
+    # split, and the tuned plan is correct
+    sizes = [m for m in TWO_LEVEL for _ in range(4)] + [640] * 40
+    plan, f, g, off, h = run_plan(dc, sizes, 44, flags=1)
+    full = sum(1 << size_code_of(m) for m in TWO_LEVEL)
+    v = plan.variants()
+    assert v is not None and (v & ~full) == 0
+    check_all(sizes, f, g, off, h)
