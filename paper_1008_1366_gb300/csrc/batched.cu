@@ -455,7 +455,10 @@ dc_status make_chunks(dc_batched_plan* p, int n) {
   free_chunks(p);
   auto& c = p->chunks;
   n = std::max(1, std::min(n, p->n));
-  const int flags = p->flags & ~DC_PLAN_ONE_PER_LAUNCH;
+  // Chunk plans on the fixed-shape engine take the plan's split variants
+  // instead of tuning their own: the split changes the rounding, and a
+  // host-to-host call gives the device-to-device call's result bit for bit.
+  const int flags = p->flags & ~(DC_PLAN_ONE_PER_LAUNCH | (p->fx ? DC_PLAN_AUTOTUNE : 0));
   int32_t i = 0;
   for (int k = 0; k < n && i < p->n; ++k) {
     const int64_t goal = p->total * (k + 1) / n;
@@ -463,7 +466,13 @@ dc_status make_chunks(dc_batched_plan* p, int n) {
     while (j < p->n && (p->off_host[j] < goal || k == n - 1)) ++j;
     dc_batched_plan* q = nullptr;
     dc_status st = dc_batched_plan_create(p->m_host.data() + i, j - i, p->dtype, flags, &q);
-    if (st != DC_OK) { free_chunks(p); return st; }
+    if (st == DC_OK && p->fx && q->fx && p->inst_first.empty() && p->fx_sched.variants)
+      st = dc_batched_plan_set_variants(q, p->fx_sched.variants);
+    if (st != DC_OK) {
+      if (q) dc_batched_plan_destroy(q);
+      free_chunks(p);
+      return st;
+    }
     c.plans.push_back(q);
     c.first.push_back(i);
     c.work = std::max(c.work, q->work);
@@ -676,6 +685,7 @@ dc_status dc_batched_plan_set_variants(dc_batched_plan* p, uint32_t mask) {
   dc_status st = fx_rebuild(p, ms.data(), p->n, p->off_host, sc);
   if (st != DC_OK) return st;
   p->fx_sched = sc;
+  free_chunks(p);   // the host pipeline's chunk plans follow the new variants
   return DC_OK;
 }
 

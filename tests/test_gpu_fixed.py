@@ -391,3 +391,25 @@ def test_autotuned_variants_valid(dc):
     v = plan.variants()
     assert v is not None and (v & ~full) == 0
     check_all(sizes, f, g, off, h)
+
+
+def test_host_pipeline_follows_variants(dc):
+    # the host-to-host pipeline's chunk plans run the plan's split variants,
+    # so its result stays the device path's bits when the variants change
+    sizes = [65536] * 2 + [10240] * 4 + [12288] * 3 + [640] * 30
+    f, g, off = synthetic.batched_inputs(sizes, 45)
+    plan = dc.BatchedPlan(sizes, dtype=torch.complex64)
+    df0 = torch.tensor(f, dtype=torch.complex64, device="cuda")
+    dg0 = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    hf = torch.tensor(f, dtype=torch.complex64).pin_memory()
+    hg = torch.tensor(g, dtype=torch.complex64).pin_memory()
+    for mask in (0, 0xFFFFFFFF, 1 << size_code_of(10240)):
+        plan.set_variants(mask)
+        ref = plan(df0, dg0).cpu()
+        hh = torch.zeros_like(hf).pin_memory()
+        df, dg, dh = (torch.empty_like(df0) for _ in range(3))
+        work = plan.host_workspace(3, df.device)
+        plan.run_from_host(hf, hg, hh, df, dg, dh, work, 3)
+        torch.cuda.synchronize()
+        assert torch.equal(hh, ref), hex(mask)
+        check_all(sizes, f, g, off, hh.numpy())
