@@ -337,8 +337,9 @@ dc_status dc_batched_plan_set_task_units(dc_batched_plan* plan, int32_t units);
  * counterpart in the paper: a tile-shape choice of this engine).  A size m of
  * the set above 2^12 (3*2^11, 5*2^10) runs its m-point sub-transforms as
  * L1-point rows and L2-point columns, m = L1 * L2; variant 0 takes L2 = 128
- * up to m = 32768 and 256 above, variant 1 the other of the two, which
- * changes the row length, the threads per row and the column tile width.
+ * up to m = 32768 and 256 above, variant 1 takes L2 = 64 for 8192, 12288
+ * and 10240 and the other of 128 and 256 for the rest, which changes the
+ * row length, the threads per row and the column tile width.
  * Bit c of *mask is set when the size with size code c (the position of m
  * in 64, 128, ..., 65536, 96, ..., 49152, 80, ..., 40960) runs variant 1;
  * dc_batched_plan_describe reports the resulting L1, L2 and tile width.

@@ -146,7 +146,7 @@ float time_cfg(const CfgDev& c, int count, int ds, const void* f, const void* g,
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   std::vector<float> t;
-  for (int rep = 0; rep < 4; ++rep) {
+  for (int rep = 0; rep <= reps; ++rep) {
     cudaMemsetAsync(dwork.p, 0, sizeof(WorkHeader), s);
     cudaEventRecord(e0, s);
     if (launch_conv1d(K_COMPLEX, ds, a, grid, c.smem, s) != DC_OK) break;
@@ -300,7 +300,8 @@ dc_status fx_launch(const dc_batched_plan* p, const void* f, const void* g, void
 }
 
 // Times the whole batch on scratch buffers (median of three after a warm-up, ms).
-float fx_time(dc_batched_plan* p, cudaStream_t s) {
+// median time of a launch of plan p (one untimed launch, then `reps`)
+float fx_time(dc_batched_plan* p, cudaStream_t s, int reps = 3) {
   DevBuf f, g, h, w;
   const size_t bytes = (size_t)p->total * (size_t)p->ds;
   if (cudaMalloc(&f.p, bytes) != cudaSuccess || cudaMalloc(&g.p, bytes) != cudaSuccess ||
@@ -312,7 +313,7 @@ float fx_time(dc_batched_plan* p, cudaStream_t s) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   std::vector<float> t;
-  for (int rep = 0; rep < 4; ++rep) {
+  for (int rep = 0; rep <= reps; ++rep) {
     cudaEventRecord(e0, s);
     if (fx_launch(p, f.p, g.p, h.p, w.p, s) != DC_OK) break;
     cudaEventRecord(e1, s);
@@ -325,9 +326,9 @@ float fx_time(dc_batched_plan* p, cudaStream_t s) {
   cudaEventDestroy(e1);
   int32_t st[2] = {0, 0};
   cudaMemcpy(st, w.p, sizeof(st), cudaMemcpyDeviceToHost);
-  if (cudaGetLastError() != cudaSuccess || t.size() < 3 || st[0] != 0) return -1;
+  if (cudaGetLastError() != cudaSuccess || (int)t.size() < reps || st[0] != 0) return -1;
   std::sort(t.begin(), t.end());
-  return t[1];
+  return t[t.size() / 2];
 }
 
 // Plain mode: the queues of one-instance plans, concatenated in instance
@@ -407,7 +408,8 @@ dc_status create_fixed(dc_batched_plan* p, const int64_t* m, int32_t n, const st
       for (int v = 0; v < 2; ++v) {
         fx::Schedule sc = dflt;
         sc.variants = (uint32_t)v << c;
-        if (fx_rebuild(p, mc.data(), (int32_t)mc.size(), oc, sc) == DC_OK) tv[v] = fx_time(p, s);
+        // short launches: more repetitions for a stable median
+        if (fx_rebuild(p, mc.data(), (int32_t)mc.size(), oc, sc) == DC_OK) tv[v] = fx_time(p, s, 9);
       }
       if (tv[0] > 0 && tv[1] > 0 && tv[1] < 0.99f * tv[0]) vmask |= 1u << c;
     }

@@ -99,9 +99,13 @@ __host__ __device__ constexpr int family_E(int L) {
 }
 __host__ __device__ constexpr bool is_level1(int m) { return m <= kThreads * family_E(m); }
 // Two-level split m = L1 L2 (L2: the column transforms' length).  Variant 0
-// takes L2 = 128 up to m = 32768 and 256 above; variant 1 the other one of
-// the two (the autotuner picks per size, FP32 binary complex plans only).
-__host__ __device__ constexpr int l2_cols(int m, int v = 0) { return (m <= 32768) != (v == 1) ? 128 : 256; }
+// takes L2 = 128 up to m = 32768 and 256 above; variant 1 takes 64 for the
+// smallest two-level size of each family (8192, 12288, 10240) and
+// otherwise the other one of 128 and 256 (the autotuner picks per size,
+// FP32 binary complex plans only).
+__host__ __device__ constexpr int l2_cols(int m, int v = 0) {
+  return v == 0 ? (m <= 32768 ? 128 : 256) : (m <= 12288 ? 64 : (m <= 32768 ? 256 : 128));
+}
 __host__ __device__ constexpr int l2_rows(int m, int v = 0) { return m / l2_cols(m, v); }   // L1
 // column transforms: 16 elements per thread where the tile width divides
 // the row length, else 8; tile width W = columns per block-wide tile

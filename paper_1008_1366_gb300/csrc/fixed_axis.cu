@@ -7,8 +7,9 @@
 //   centered (q = 3): axis holds 2m-1 values, origin at m-1; residue
 //            r = -1, 0, 1 input w_{k,r} of Eqs. (2.4)-(2.5); forward Eq. (2.6)
 //            for k = -m+1..m-1.
-// A block of 256 threads owns one outer index and a tile of W consecutive
-// inner indices (columns); W = 256 E / m, T = m / E threads per column.
+// A block of NT threads (256; 512 for complex axes of 2048 points and more)
+// owns one outer index and a tile of W consecutive inner indices (columns);
+// W = NT E / m, T = m / E threads per column.
 // Complex axes take E = 16; centered axes, whose tiles also hold the 2m-1
 // staged input rows, take E = 8 up to m = 512 (half the columns, half the
 // shared memory, twice the resident blocks), where a tile row still fills
@@ -30,11 +31,15 @@ namespace DC_FX_P {
 
 namespace {
 
+// Complex axes of 2048 and more points run blocks of 512 threads, so that a
+// tile row spans W >= 2 (FP32: 4) columns and its loads use whole 32-byte
+// sectors; the centered ones, whose tiles also stage 2m-1 rows, keep 256.
 template <int L, bool CEN> struct AxisShape {
+  static constexpr int NT = !CEN && L >= 2048 ? 512 : kThreads;
   static constexpr int E = CEN && L <= 512 ? 8 : 16;
   static constexpr int T = L / E;
-  static constexpr int W = kThreads * E / L;
-  static_assert(L % E == 0 && W >= 1 && W * T == kThreads, "axis tile covers the block");
+  static constexpr int W = NT * E / L;
+  static_assert(L % E == 0 && W >= 1 && W * T == NT, "axis tile covers the block");
 };
 
 __host__ __device__ constexpr int axis_ceil_log2(int x) {
@@ -75,19 +80,19 @@ __device__ __forceinline__ C sym_part(C v, C u, bool dbl) {
   return s;
 }
 
-template <int TN>
+template <int TN, int NT>
 __device__ __forceinline__ Roots<C> fill_roots(const AxisArgs& a, C* rts) {
   constexpr int sh = (axis_ceil_log2(TN) + 1) / 2, nlo = 1 << sh;
   constexpr int cnt = nlo + (TN + nlo - 1) / nlo;
   static_assert(cnt <= kRootsMax, "root tables fit their reservation");
   const C* tab = (const C*)a.tw;
-  for (int e = threadIdx.x; e < cnt; e += kThreads) rts[e] = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
+  for (int e = threadIdx.x; e < cnt; e += NT) rts[e] = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
   __syncthreads();
   return Roots<C>{rts, rts + nlo, sh, nlo - 1};
 }
 
 template <int L, bool CEN>
-__global__ void __launch_bounds__(kThreads) axis_bwd_kernel(const __grid_constant__ AxisArgs a) {
+__global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_bwd_kernel(const __grid_constant__ AxisArgs a) {
   using S = AxisShape<L, CEN>;
   constexpr int E = S::E, W = S::W, TN = (CEN ? 3 : 2) * L, nin = CEN ? 2 * L - 1 : L;
   using K = Stage<L, E, 0, false>;
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) axis_bwd_kernel(const __grid_constan
   C* rts = (C*)smem_raw;
   C* buf = rts + kRootsMax;
   C* stg = buf + W * L;   // centered: the staged input tile, nin rows of W
-  const Roots<C> rt = fill_roots<TN>(a, rts);
+  const Roots<C> rt = fill_roots<TN, S::NT>(a, rts);
   const int z = blockIdx.y;
   const C* in = (const C*)a.in[z];
   const bool dbl = (a.dbl_mask >> z) & 1;
@@ -148,12 +153,12 @@ __global__ void __launch_bounds__(kThreads) axis_bwd_kernel(const __grid_constan
     // the self-conjugate set is made once, and the loads of its rows are
     // independent of one another.
     {
-      static_assert(kThreads % W == 0, "a thread keeps its column while staging");
+      static_assert(S::NT % W == 0, "a thread keeps its column while staging");
       int64_t mi = 0;
       const bool sym = act && on_selfconj(a, col, &mi);
       const C* base = in + o * (int64_t)nin * a.inner;
 #pragma unroll 8
-      for (int j = i; j < nin; j += kThreads / W) {
+      for (int j = i; j < nin; j += S::NT / W) {
         C v = act ? base[(int64_t)j * a.inner + col] : zero;
         if (sym) v = sym_part(v, base[(int64_t)(nin - 1 - j) * a.inner + mi], dbl);
         stg[j * W + c] = v;
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) axis_bwd_kernel(const __grid_constan
 }
 
 template <int L, bool CEN>
-__global__ void __launch_bounds__(kThreads) axis_fwd_kernel(const __grid_constant__ AxisArgs a) {
+__global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_fwd_kernel(const __grid_constant__ AxisArgs a) {
   using S = AxisShape<L, CEN>;
   constexpr int E = S::E, W = S::W, q = CEN ? 3 : 2, TN = q * L, nout = CEN ? 2 * L - 1 : L;
   using K = Stage<L, E, 0, true>;
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) axis_fwd_kernel(const __grid_constan
   C* rts = (C*)smem_raw;
   C* buf = rts + kRootsMax;
   C* H = buf + W * L;   // centered: the recombined outputs, nout rows of W
-  const Roots<C> rt = fill_roots<TN>(a, rts);
+  const Roots<C> rt = fill_roots<TN, S::NT>(a, rts);
   const int z = blockIdx.y;
   const int64_t tiles = (a.inner + W - 1) / W;
   const int64_t o = blockIdx.x / tiles;
@@ -273,11 +278,11 @@ __global__ void __launch_bounds__(kThreads) axis_fwd_kernel(const __grid_constan
     }
     // one scaled write of the tile (coalesced rows of W); a thread keeps its
     // column, whose scale sc was set above
-    static_assert(kThreads % W == 0, "a thread keeps its column while writing");
+    static_assert(S::NT % W == 0, "a thread keeps its column while writing");
     C* out = (C*)a.fout[z] + o * (int64_t)nout * a.inner + col;
     if (act) {
 #pragma unroll 8
-      for (int j = i; j < nout; j += kThreads / W) out[(int64_t)j * a.inner] = cscale(H[j * W + c], sc);
+      for (int j = i; j < nout; j += S::NT / W) out[(int64_t)j * a.inner] = cscale(H[j * W + c], sc);
     }
   }
 }
@@ -292,7 +297,7 @@ dc_status launch_LC(bool forward, const AxisArgs& a, int narrays, cudaStream_t s
   dim3 grid((unsigned)tiles, (unsigned)narrays);
   auto k = forward ? axis_fwd_kernel<L, CEN> : axis_bwd_kernel<L, CEN>;
   DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k<<<grid, kThreads, smem, s>>>(a);
+  k<<<grid, S::NT, smem, s>>>(a);
   DC_CUDA_TRY(cudaGetLastError());
   return DC_OK;
 }

@@ -322,8 +322,9 @@ def size_code_of(m):
 
 
 def test_split_variants_every_two_level_size(dc):
-    # variant 1 of the two-level split (L2 = 256 up to m = 32768, 128
-    # above): every two-level size, several instances each, against the
+    # variant 1 of the two-level split (L2 = 64 for the smallest two-level
+    # size of each family, else 256 up to m = 32768 and 128 above): every
+    # two-level size, several instances each, against the
     # oracle; describe reports the swapped split and the mask reads back
     sizes = [m for m in TWO_LEVEL for _ in range(3)] + [640] * 20 + [64] * 70
     rng = np.random.default_rng(41)
@@ -339,7 +340,8 @@ def test_split_variants_every_two_level_size(dc):
     for m in TWO_LEVEL:
         l1, l2 = before[m][3], before[m][4]
         assert l1 * l2 == m and after[m][3] * after[m][4] == m
-        assert after[m][4] == (256 if l2 == 128 else 128), (m, before[m], after[m])
+        want = 64 if m in (8192, 12288, 10240) else (256 if l2 == 128 else 128)
+        assert after[m][4] == want, (m, before[m], after[m])
     assert after[640] == before[640] and after[64] == before[64]
     tf = torch.tensor(f, dtype=torch.complex64, device="cuda")
     tg = torch.tensor(g, dtype=torch.complex64, device="cuda")
