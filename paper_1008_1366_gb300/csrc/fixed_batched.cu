@@ -48,6 +48,12 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
+// one element (8 or 16 bytes) global-to-shared, asynchronously
+__device__ __forceinline__ void cp_async_elem(C* dst, const C* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(C) == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -904,10 +910,14 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
       // and the size's stage tables (a contiguous copy) behind its task data
       const C* stab = (const C*)a.stab[code];
       C* sdst = (C*)(smem_raw + a.stab_off[code]);
+      // (asynchronous copies: a thread's entries are all in flight at once,
+      // one L2 round trip per switch instead of one per entry it copies)
       for (int e = threadIdx.x; e < cnt + a.stab_n[code]; e += kThreads) {
-        if (e < cnt) (e < nlo ? rts[e] : hi[e - nlo]) = __ldg(tab + (e < nlo ? e : (e - nlo) << sh));
-        else sdst[e - cnt] = __ldg(stab + (e - cnt));
+        if (e < cnt) cp_async_elem(e < nlo ? rts + e : hi + (e - nlo), tab + (e < nlo ? e : (e - nlo) << sh));
+        else cp_async_elem(sdst + (e - cnt), stab + (e - cnt));
       }
+      cp_async_commit();
+      cp_async_wait_all();
       rt = Roots<C>{rts, hi, sh, nlo - 1};
       cur = code;
       __syncthreads();
