@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(512) axis_backward_kernel(AxisArgs a) {
     }
     __syncthreads();
     fft_smem<1>(sm + cc, w, a.p, ci, act, tw, a.TN);
-    C* out = (C*)a.out[z * 3 + ri];
+    C* out = (C*)a.out[z * kAxisQ + ri];
     for (int e = tid; e < L * w; e += T) {
       const int k = e / w, c = e - k * w;
       const int64_t i = i0 + c;
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(512) axis_forward_kernel(AxisArgs a) {
   using R = decltype(sm[0].x);
   for (int ri = 0; ri < q; ++ri) {
     const int r = a.centered == 1 ? ri - 1 : ri;
-    const C* src = (const C*)a.fin[z * 3 + ri];
+    const C* src = (const C*)a.fin[z * kAxisQ + ri];
     for (int e = tid; e < L * w; e += T) {
       const int k = e / w, c = e - k * w;
       const int64_t i = i0 + c;
@@ -196,7 +196,7 @@ dc_status launch_axis(bool forward, int dsize, const AxisArgs& a, int narrays, c
   // axis lengths with compile-time code (fixed_axis.cu) run there
   const dc_status fst = dsize == 8 ? fx::f32::launch_axis_fixed(forward, a, narrays, s)
                                    : fx::f64::launch_axis_fixed(forward, a, narrays, s);
-  if (fst != DC_ERR_SIZE) return fst;
+  if (fst != DC_ERR_SIZE || a.centered == 3) return fst;   // four residues: compile-time lengths only
   const int64_t tiles = a.outer * ((a.inner + a.w - 1) / a.w);
   if (tiles < 1 || narrays < 1) return DC_OK;
   if (tiles > 0x7fffffff) return DC_ERR_SIZE;

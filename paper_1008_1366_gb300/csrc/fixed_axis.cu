@@ -31,11 +31,15 @@ namespace DC_FX_P {
 
 namespace {
 
-// Complex axes of 2048 and more points run blocks of 512 threads, so that a
-// tile row spans W >= 2 (FP32: 4) columns and its loads use whole 32-byte
-// sectors; the centered ones, whose tiles also stage 2m-1 rows, keep 256.
-template <int L, bool CEN> struct AxisShape {
-  static constexpr int NT = !CEN && L >= 2048 ? 512 : kThreads;
+// Q residues: 2 complex (N = 2m), 3 centered (N = 3m), 4 the ternary
+// kind's N = 4m taken as four m-point residues (below).  Complex axes of
+// 2048 and more points run blocks of 512 threads, so that a tile row spans
+// W >= 2 (FP32: 4) columns and its loads use whole 32-byte sectors; so do
+// the FP32 four-residue axes there (their staged rows still fit); the
+// centered ones keep 256.
+template <int L, int Q> struct AxisShape {
+  static constexpr bool CEN = Q >= 3;
+  static constexpr int NT = L >= 2048 && (Q == 2 || (Q == 4 && !kDouble)) ? 512 : kThreads;
   static constexpr int E = CEN && L <= 512 ? 8 : 16;
   static constexpr int T = L / E;
   static constexpr int W = NT * E / L;
@@ -50,9 +54,9 @@ __host__ __device__ constexpr int axis_ceil_log2(int x) {
 
 // shared memory: roots, transform buffer (W L), and for centered axes the
 // staged input or recombination buffer ((2m-1) W)
-template <int L, bool CEN> constexpr int axis_smem_bytes() {
-  using S = AxisShape<L, CEN>;
-  return (kRootsMax + S::W * L + (CEN ? (2 * L - 1) * S::W : 0)) * (int)sizeof(C);
+template <int L, int Q> constexpr int axis_smem_bytes() {
+  using S = AxisShape<L, Q>;
+  return (kRootsMax + S::W * L + (S::CEN ? (2 * L - 1) * S::W : 0)) * (int)sizeof(C);
 }
 
 __device__ __forceinline__ bool on_selfconj(const AxisArgs& a, int64_t i, int64_t* mirror) {
@@ -91,10 +95,11 @@ __device__ __forceinline__ Roots<C> fill_roots(const AxisArgs& a, C* rts) {
   return Roots<C>{rts, rts + nlo, sh, nlo - 1};
 }
 
-template <int L, bool CEN>
-__global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_bwd_kernel(const __grid_constant__ AxisArgs a) {
-  using S = AxisShape<L, CEN>;
-  constexpr int E = S::E, W = S::W, TN = (CEN ? 3 : 2) * L, nin = CEN ? 2 * L - 1 : L;
+template <int L, int Q>
+__global__ void __launch_bounds__(AxisShape<L, Q>::NT) axis_bwd_kernel(const __grid_constant__ AxisArgs a) {
+  using S = AxisShape<L, Q>;
+  constexpr bool CEN = S::CEN;
+  constexpr int E = S::E, W = S::W, TN = Q * L, nin = CEN ? 2 * L - 1 : L;
   using K = Stage<L, E, 0, false>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* rts = (C*)smem_raw;
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_bwd_kernel(const _
           const int e = b * K::R + q;
           v[e] = r ? cmul(raw[e], rt.at(pos<L, E, 0, false>(i, b, q))) : raw[e];
         }
-      C* out = (C*)a.out[z * 3 + r] + o * (int64_t)L * a.inner + col;
+      C* out = (C*)a.out[z * kAxisQ + r] + o * (int64_t)L * a.inner + col;
       column<L, E, W, TN, false>(v, i, buf + c, rt, [&](int j, int, C y) {
         if (act) out[(int64_t)j * a.inner] = y;
       });
@@ -166,32 +171,39 @@ __global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_bwd_kernel(const _
     }
     __syncthreads();
 #pragma unroll 1
-    for (int ri = 0; ri < 3; ++ri) {
-      const int r = ri - 1;
+    for (int ri = 0; ri < Q; ++ri) {
+      const int r = Q == 3 ? ri - 1 : ri;
       C v[E];
 #pragma unroll
       for (int b = 0; b < K::NB; ++b)
 #pragma unroll
         for (int q = 0; q < K::R; ++q) {
-          // w_{k,r} = U_0 at k = 0, else zeta_{3m}^{rk} (U_k + zeta_3^{-r} U_{k-m})
+          // w_{k,r} = U_0 at k = 0, else zeta_{Qm}^{rk} (U_k + zeta_Q^{-r} U_{k-m})
+          // (Q = 4: the ternary kind's U_{-m} = 0, so k = 0 holds U_0 alone)
           const int k = pos<L, E, 0, false>(i, b, q);
           C x = stg[(k + L - 1) * W + c];
           if (k > 0) {
             const C u = stg[(k - 1) * W + c];
             if (r == 0) {
               x = cadd(x, u);
-            } else {
+            } else if constexpr (Q == 3) {
               C z3;
               z3.x = (Real)-0.5;
               z3.y = (Real)(-r) * (Real)0.86602540378443864676;
               x = cadd(x, cmul(u, z3));
               const C t = rt.at(k);
               x = r > 0 ? cmul(x, t) : cmulc(x, t);
+            } else {
+              // zeta_4^{-r} = (-i)^r
+              C z;
+              z.x = r == 1 ? u.y : (r == 2 ? -u.x : -u.y);
+              z.y = r == 1 ? -u.x : (r == 2 ? -u.y : u.x);
+              x = cmul(cadd(x, z), rt.at(r * k));
             }
           }
           v[b * K::R + q] = x;
         }
-      C* out = (C*)a.out[z * 3 + ri] + o * (int64_t)L * a.inner + col;
+      C* out = (C*)a.out[z * kAxisQ + ri] + o * (int64_t)L * a.inner + col;
       column<L, E, W, TN, false>(v, i, buf + c, rt, [&](int j, int, C y) {
         if (act) out[(int64_t)j * a.inner] = y;
       });
@@ -200,10 +212,11 @@ __global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_bwd_kernel(const _
   }
 }
 
-template <int L, bool CEN>
-__global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_fwd_kernel(const __grid_constant__ AxisArgs a) {
-  using S = AxisShape<L, CEN>;
-  constexpr int E = S::E, W = S::W, q = CEN ? 3 : 2, TN = q * L, nout = CEN ? 2 * L - 1 : L;
+template <int L, int Q>
+__global__ void __launch_bounds__(AxisShape<L, Q>::NT) axis_fwd_kernel(const __grid_constant__ AxisArgs a) {
+  using S = AxisShape<L, Q>;
+  constexpr bool CEN = S::CEN;
+  constexpr int E = S::E, W = S::W, q = Q, TN = q * L, nout = CEN ? 2 * L - 1 : L;
   using K = Stage<L, E, 0, true>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* rts = (C*)smem_raw;
@@ -229,7 +242,7 @@ __global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_fwd_kernel(const _
     C vin[2][E];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      const C* src = (const C*)a.fin[z * 3 + r] + o * (int64_t)L * a.inner + col;
+      const C* src = (const C*)a.fin[z * kAxisQ + r] + o * (int64_t)L * a.inner + col;
 #pragma unroll
       for (int b = 0; b < K::NB; ++b)
 #pragma unroll
@@ -246,9 +259,9 @@ __global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_fwd_kernel(const _
     });
   } else {
 #pragma unroll 1
-    for (int ri = 0; ri < 3; ++ri) {
-      const int r = ri - 1;
-      const C* src = (const C*)a.fin[z * 3 + ri] + o * (int64_t)L * a.inner + col;
+    for (int ri = 0; ri < Q; ++ri) {
+      const int r = Q == 3 ? ri - 1 : ri;
+      const C* src = (const C*)a.fin[z * kAxisQ + ri] + o * (int64_t)L * a.inner + col;
       C v[E];
 #pragma unroll
       for (int b = 0; b < K::NB; ++b)
@@ -261,11 +274,18 @@ __global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_fwd_kernel(const _
       column<L, E, W, TN, true>(v, i, buf + c, rt, [&](int kk, int, C y) {
         C hi = y, lo = y;
         if (r != 0) {
-          // k = kk >= 0: zeta_{3m}^{-r kk}; k = kk - m < 0: zeta_{3m}^{-r (kk - m)}
-          const C t = rt.at(kk);
-          hi = r > 0 ? cmulc(y, t) : cmul(y, t);
-          const C u = rt.at(L - kk);
-          lo = r > 0 ? cmul(y, u) : cmulc(y, u);
+          if constexpr (Q == 3) {
+            // k = kk >= 0: zeta_{3m}^{-r kk}; k = kk - m < 0: zeta_{3m}^{-r (kk - m)}
+            const C t = rt.at(kk);
+            hi = r > 0 ? cmulc(y, t) : cmul(y, t);
+            const C u = rt.at(L - kk);
+            lo = r > 0 ? cmul(y, u) : cmulc(y, u);
+          } else {
+            // k = kk: zeta_{4m}^{-r kk}; k = kk - m: that times zeta_4^r = i^r
+            hi = cmulc(y, rt.at(r * kk));
+            lo.x = r == 1 ? -hi.y : (r == 2 ? -hi.x : hi.y);
+            lo.y = r == 1 ? hi.x : (r == 2 ? -hi.y : -hi.x);
+          }
         }
         C* h1 = &H[(kk + L - 1) * W + c];
         *h1 = ri ? cadd(*h1, hi) : hi;
@@ -287,15 +307,15 @@ __global__ void __launch_bounds__(AxisShape<L, CEN>::NT) axis_fwd_kernel(const _
   }
 }
 
-template <int L, bool CEN>
+template <int L, int Q>
 dc_status launch_LC(bool forward, const AxisArgs& a, int narrays, cudaStream_t s) {
-  using S = AxisShape<L, CEN>;
+  using S = AxisShape<L, Q>;
   const int64_t tiles = a.outer * ((a.inner + S::W - 1) / S::W);
   if (tiles < 1 || narrays < 1) return DC_OK;
   if (tiles > 0x7fffffff) return DC_ERR_SIZE;
-  constexpr int smem = axis_smem_bytes<L, CEN>();
+  constexpr int smem = axis_smem_bytes<L, Q>();
   dim3 grid((unsigned)tiles, (unsigned)narrays);
-  auto k = forward ? axis_fwd_kernel<L, CEN> : axis_bwd_kernel<L, CEN>;
+  auto k = forward ? axis_fwd_kernel<L, Q> : axis_bwd_kernel<L, Q>;
   DC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   k<<<grid, S::NT, smem, s>>>(a);
   DC_CUDA_TRY(cudaGetLastError());
@@ -304,14 +324,15 @@ dc_status launch_LC(bool forward, const AxisArgs& a, int narrays, cudaStream_t s
 
 template <int L>
 dc_status launch_L(bool forward, const AxisArgs& a, int narrays, cudaStream_t s) {
-  return a.centered ? launch_LC<L, true>(forward, a, narrays, s) : launch_LC<L, false>(forward, a, narrays, s);
+  if (a.centered == 3) return launch_LC<L, 4>(forward, a, narrays, s);
+  return a.centered ? launch_LC<L, 3>(forward, a, narrays, s) : launch_LC<L, 2>(forward, a, narrays, s);
 }
 
 }  // namespace
 
 // DC_ERR_SIZE when the axis length is not one this file compiles
 dc_status launch_axis_fixed(bool forward, const AxisArgs& a, int narrays, cudaStream_t s) {
-  if (a.centered == 2) return DC_ERR_SIZE;   // ternary axes: the runtime-shaped kernels (axis.cu)
+  if (a.centered == 2) return DC_ERR_SIZE;   // two 2m-point residues: the runtime-shaped kernels (axis.cu)
   switch (a.m) {
     case 64: return launch_L<64>(forward, a, narrays, s);
     case 128: return launch_L<128>(forward, a, narrays, s);

@@ -68,7 +68,8 @@ struct Md {
 
 int smem_cap() { return device_info().smem_optin - kStaticSmemReserve; }
 
-// mode: 0 complex, 1 centered (q = 3), 2 centered ternary (q = 2, length 2m)
+// mode: 0 complex, 1 centered (q = 3), 2 centered ternary (q = 2, length
+// 2m), 3 centered ternary (q = 4, length m)
 bool axis_cfg(int mode, int64_t m, int ds, bool with_table, AxisArgs* a) {
   const int emax = ds == 8 ? 30 : 15;
   FftPlan p;
@@ -84,7 +85,7 @@ bool axis_cfg(int mode, int64_t m, int ds, bool with_table, AxisArgs* a) {
   a->centered = mode;
   a->w = w;
   a->p = p;
-  a->TN = (int32_t)((mode == 2 ? 4 : mode == 1 ? 3 : 2) * m);
+  a->TN = (int32_t)((mode >= 2 ? 4 : mode == 1 ? 3 : 2) * m);
   if (with_table) {
     const void* tw = nullptr;
     if (get_root_table(a->TN, ds, &tw) != DC_OK) return false;
@@ -108,16 +109,20 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   md->herm = pk == DC_KIND_HERMITIAN || pk == DC_KIND_HERMITIAN_ADJOINT || pk == DC_KIND_HERMITIAN_DOT2 || md->tern;
   md->adj = pk == DC_KIND_COMPLEX_ADJOINT || pk == DC_KIND_HERMITIAN_ADJOINT;
   if (pk < 0 || pk > DC_KIND_HERMITIAN_DOT2) return DC_ERR_ARG;
-  md->qa = md->tern ? 2 : (md->herm ? 3 : 2);
+  // outer axes: centered for Hermitian data; for the ternary kind N = 4m
+  // per axis (Sec. 4.1), as four m-point residues where the compile-time
+  // axis kernels take every outer length (the residue inputs fold U_k and
+  // U_{k-m} like the centered case, with zeta_4 for zeta_3), else as two
+  // residues of 2m points
+  const bool tern4 = md->tern && fixed_axis_len(dims[0]) && (ndim == 2 || fixed_axis_len(dims[1]));
+  const int amode = md->tern ? (tern4 ? 3 : 2) : (md->herm ? 1 : 0);
+  md->qa = axis_q(amode);
   md->narr = dot ? 4 : (md->adj || md->tern ? 3 : 2);
   md->nout = md->adj ? 2 : 1;
   md->row_kind = md->tern ? K_TERNARY
                  : dot ? (md->herm ? K_HERMITIAN_DOT2 : K_COMPLEX_DOT2)
                        : md->herm ? (md->adj ? K_HERMITIAN_PAIR : K_HERMITIAN)
                                   : (md->adj ? K_COMPLEX_ADJ : K_COMPLEX);
-  // outer axes: centered for Hermitian data, of twice the length for the
-  // ternary kind (N = 4m per axis, Sec. 4.1)
-  const int amode = md->tern ? 2 : (md->herm ? 1 : 0);
   const int64_t mx = md->m[0], my = md->m[1], mlast = md->m[ndim - 1];
   md->Lx = axis_len(amode, (int)mx);
   md->Ly = ndim == 3 ? axis_len(amode, (int)my) : 0;
@@ -317,7 +322,7 @@ dc_status md_run(int pk, int ndim, const int64_t* dims, int ds, const void* cons
   ax.dbl_mask = (pk == DC_KIND_HERMITIAN_ADJOINT) ? 1 : 0;
   for (int z = 0; z < md.narr; ++z) {
     ax.in[z] = ins[z];
-    for (int r = 0; r < qa; ++r) ax.out[z * 3 + r] = xres(z, r);
+    for (int r = 0; r < qa; ++r) ax.out[z * kAxisQ + r] = xres(z, r);
   }
   if ((st = launch_axis(false, ds, ax, md.narr, s)) != DC_OK) return st;
 
@@ -338,7 +343,7 @@ dc_status md_run(int pk, int ndim, const int64_t* dims, int ds, const void* cons
       ay.inner = mz;
       for (int z = 0; z < md.narr; ++z) {
         ay.in[z] = X + ((size_t)z * qa * md.nx + (size_t)s0 * md.sx) * ds;
-        for (int r = 0; r < qa; ++r) ay.out[z * 3 + r] = yres(z, r);
+        for (int r = 0; r < qa; ++r) ay.out[z * kAxisQ + r] = yres(z, r);
       }
       if ((st = launch_axis(false, ds, ay, md.narr, s)) != DC_OK) return st;
       const void* rin[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -350,7 +355,7 @@ dc_status md_run(int pk, int ndim, const int64_t* dims, int ds, const void* cons
       yf.outer = Sc;
       yf.inner = mz;
       for (int o = 0; o < md.nout; ++o) {
-        for (int r = 0; r < qa; ++r) yf.fin[o * 3 + r] = yres(oslot0 + o, r);
+        for (int r = 0; r < qa; ++r) yf.fin[o * kAxisQ + r] = yres(oslot0 + o, r);
         yf.fout[o] = X + ((size_t)(oslot0 + o) * qa * md.nx + (size_t)s0 * md.sx) * ds;
       }
       if ((st = launch_axis(true, ds, yf, md.nout, s)) != DC_OK) return st;
@@ -366,7 +371,7 @@ dc_status md_run(int pk, int ndim, const int64_t* dims, int ds, const void* cons
   xf.proj_ny = ax.proj_ny;
   xf.halve_mask = (pk == DC_KIND_HERMITIAN_ADJOINT) ? 3 : 0;
   for (int o = 0; o < md.nout; ++o) {
-    for (int r = 0; r < qa; ++r) xf.fin[o * 3 + r] = xres(oslot0 + o, r);
+    for (int r = 0; r < qa; ++r) xf.fin[o * kAxisQ + r] = xres(oslot0 + o, r);
     xf.fout[o] = outs[o];
   }
   return launch_axis(true, ds, xf, md.nout, s);

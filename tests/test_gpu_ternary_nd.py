@@ -1,9 +1,11 @@
 """GPU parity of the 2D and 3D centered Hermitian ternary convolutions
-(Sec. 4: Function tconv2, the outer axes padded implicitly to N = 4m with
-two residues of 2m-point sub-transforms, Eqs. (fft0tbackward)-(fft0tforward);
-the last axis by the 1D ternary rows of Sec. 4.2) against the FP64 oracle,
-every output, both error bars of conftest.check_parity, both precisions;
-the paper's 4096 x 4096 shape (Fig. 9) in FP32."""
+(Sec. 4: Function tconv2, the outer axes padded implicitly to N = 4m,
+Eqs. (fft0tbackward)-(fft0tforward): as two residues of 2m-point
+sub-transforms, or, where every outer length is a power of two from 64 to
+4096, as four m-point residues; the last axis by the 1D ternary rows of
+Sec. 4.2) against the FP64 oracle, every output, both error bars of
+conftest.check_parity, both precisions; the paper's 4096 x 4096 shape
+(Fig. 9) in FP32."""
 
 import numpy as np
 import pytest
@@ -34,7 +36,9 @@ def inputs(ms, seed, alpha):
     return [synthetic.hermitian_spectrum(shape, alpha, seed + s) for s in range(3)]
 
 
-T2 = [(1, 1), (2, 2), (3, 4), (4, 4), (8, 6), (5, 9), (16, 16), (32, 24), (64, 64), (128, 96), (9, 15)]
+# (64, 64), (128, 96), (256, 40), (512, 3), (2048, 5): four m-point residues on the x axis
+T2 = [(1, 1), (2, 2), (3, 4), (4, 4), (8, 6), (5, 9), (16, 16), (32, 24), (64, 64), (128, 96), (9, 15),
+      (256, 40), (512, 3), (2048, 5)]
 
 
 @pytest.mark.parametrize("ms", T2)
@@ -46,8 +50,10 @@ def test_ternary_2d(dc, ms, dtype):
                  hermitian_scale(f, g, e))
 
 
+# (64, 64, 8), (64, 128, 6): four m-point residues on both outer axes,
+# the second in chunks of 37 slabs (the last one partial)
 @pytest.mark.parametrize("ms,spc", [((2, 2, 2), None), ((3, 4, 5), None), ((4, 4, 4), 3), ((5, 3, 8), 7),
-                                    ((8, 8, 16), None)])
+                                    ((8, 8, 16), None), ((64, 64, 8), None), ((64, 128, 6), 37)])
 @pytest.mark.parametrize("dtype", DT)
 def test_ternary_3d(dc, ms, spc, dtype):
     f, g, e = inputs(ms, 84, 11 / 6)
