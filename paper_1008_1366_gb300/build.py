@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libdealias.so")
 SOURCES = ["capi.cu", "plan.cu", "twiddle.cu", "conv1d.cu", "batched.cu", "axis.cu", "multid.cu", "noalloc.cu",
            "partition.cu", "pq.cu"]
 # the fixed-shape engine per precision: the outer-axis kernels, the batched
-# planner, and the batched kernel of each convolution kind (MODE_* 0..4) in
+# planner, and the batched kernel of each convolution kind (MODE_* 0..5) in
 # a translation unit of its own, so that the kinds compile in parallel
 _PREC = (("f", "f32", "float2"), ("d", "f64", "double2"))
 FIXED = ([("fixed_axis.cu", f"fixed_axis_{tag}.o", [f"-DDC_FX_P={ns}", f"-DDC_FX_C={c}"]) for tag, ns, c in _PREC]
@@ -27,7 +27,7 @@ FIXED = ([("fixed_axis.cu", f"fixed_axis_{tag}.o", [f"-DDC_FX_P={ns}", f"-DDC_FX
             for tag, ns, c in _PREC]
          + [("fixed_batched.cu", f"fixed_batched_m{k}_{tag}.o", [f"-DDC_FX_P={ns}", f"-DDC_FX_C={c}",
                                                                  f"-DDC_FX_MODE={k}"])
-            for k in range(5) for tag, ns, c in _PREC])
+            for k in range(6) for tag, ns, c in _PREC])
 # the fused 1D kernel, one translation unit per (kind, precision)
 INSTANCES = [(k, tag, c) for k in range(8) for tag, c in (("f", "float2"), ("d", "double2"))]
 

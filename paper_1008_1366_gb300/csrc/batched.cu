@@ -230,7 +230,7 @@ dc_status fx_upload(dc_batched_plan* p, const std::vector<int64_t>& off) {
 dc_status fx_tables(dc_batched_plan* p) {
   for (int c : p->hp.codes) {
     if (!p->tabs[c]) {
-      dc_status st = get_root_table((fx::mode_tables_3m(p->mode) ? 3 : 2) * p->ops->code_size(c), p->ds, &p->tabs[c]);
+      dc_status st = get_root_table(fx::mode_q(p->mode) * p->ops->code_size(c), p->ds, &p->tabs[c]);
       if (st != DC_OK) return st;
     }
     if (!p->stabs[c]) {
@@ -982,6 +982,13 @@ dc_status fx_hdot2_run(dc_batched_plan* p, const void* f1, const void* g1, const
   if (!p || p->mode != fx::MODE_HDOT2) return DC_ERR_ARG;
   if (work_bytes < p->work) return DC_ERR_NOMEM;
   return fx_launch(p, f1, g1, h, work, s, f2, nullptr, g2);
+}
+
+dc_status fx_tern4_run(dc_batched_plan* p, const void* f, const void* g, const void* e, void* h, void* work,
+                       size_t work_bytes, cudaStream_t s) {
+  if (!p || p->mode != fx::MODE_TERN4) return DC_ERR_ARG;
+  if (work_bytes < p->work) return DC_ERR_NOMEM;
+  return fx_launch(p, f, g, h, work, s, e);
 }
 
 dc_status fx_pair_run(dc_batched_plan* p, const void* w, const void* f, const void* g, void* df, void* dg,

@@ -35,10 +35,15 @@ enum : int32_t { T_L1 = 0, T_A = 1, T_B = 2, T_C = 3 };
 //                 vectors, Sec. 3): inputs (f1, g1, f2, g2) in (f, g, e, e2),
 //                 output f1 * g1 + f2 * g2 in h, tables of zeta_{3m},
 //                 one-level sizes only
-enum : int32_t { MODE_COMPLEX = 0, MODE_HERM = 1, MODE_TERN = 2, MODE_PAIR = 3, MODE_HDOT2 = 4 };
+//   MODE_TERN4    centered Hermitian ternary of length m (N = 4m) as four
+//                 m-point residues, inputs (f, g, e), output h, tables of
+//                 zeta_{4m}, one-level sizes only
+enum : int32_t { MODE_COMPLEX = 0, MODE_HERM = 1, MODE_TERN = 2, MODE_PAIR = 3, MODE_HDOT2 = 4, MODE_TERN4 = 5 };
 __host__ __device__ constexpr bool mode_tables_3m(int mode) {
   return mode == MODE_HERM || mode == MODE_PAIR || mode == MODE_HDOT2;
 }
+// the root table of a kind is zeta_{qm}, q = mode_q(kind)
+__host__ __device__ constexpr int mode_q(int mode) { return mode_tables_3m(mode) ? 3 : (mode == MODE_TERN4 ? 4 : 2); }
 
 // One queue entry.  kc = units << 16 | type << 8 | size code.  T_L1: a =
 // first slot of the order array, b = instance count.  T_A/T_B/T_C: a =

@@ -130,6 +130,7 @@ template <int M, int V = 0> struct Shape {
   static constexpr int total = tab_off + tab_entries * CB;
   static_assert(herm_lo <= kRootsMax, "low root table fits its reservation");
   static_assert(roots_count(2 * M) <= kRootsMax && (!l1 || herm_roots <= kRootsMax), "root tables fit");
+  static_assert(!l1 || roots_count(4 * M) <= kRootsMax, "the four-residue ternary tables fit");
   // FP32: two blocks per SM, FP64: one (228 KB per SM less 1 KB reserved per
   // block and the static shared variables)
   static_assert(total <= (233472 - kBlocksPerSM * 1024) / kBlocksPerSM - 64, "the blocks fit on an SM");
@@ -203,6 +204,57 @@ struct HermTerms {
     C q = __ldg(u + mx);
     q.y = -q.y;
     C v = cmul(cadd(p, cmul(q, z3)), tw(x, rt, 1));
+    if (x == 0) {
+      v.x = p.x;
+      v.y = 0;
+    }
+    return v;
+  }
+  __device__ __forceinline__ C out(C v, int x, const Roots<C>& rt) const { return cmul(v, tw(x, rt, -1)); }
+};
+
+// Residue r = 0..3 of a centered Hermitian ternary convolution taken as four
+// m-point residues of the N = 4m padding (Sec. 4.1's padding; the fold of
+// Sec. 2.2 with zeta_4 for zeta_3): the input at k > 0 is
+// zeta_{4m}^{rk} (U_k + zeta_4^{-r} U_{k-m}), U_{k-m} = conj U_{m-k}, and at
+// k = 0 it is U_0 (U_{-m} = 0); the output factor is zeta_{4m}^{-rk}.
+struct Tern4Terms {
+  int r;
+  C z4;   // zeta_4^{-r} = (-i)^r
+  __device__ __forceinline__ explicit Tern4Terms(int r_) : r(r_) {
+    z4.x = r_ == 0 ? (Real)1 : (r_ == 2 ? (Real)-1 : (Real)0);
+    z4.y = r_ == 1 ? (Real)-1 : (r_ == 3 ? (Real)1 : (Real)0);
+  }
+  // zeta_{4m}^{s r k} (r k < 3m: inside the table of zeta_{4m})
+  __device__ __forceinline__ C tw(int x, const Roots<C>& rt, int s) const {
+    C t = rt.at(r * x);
+    if (s < 0) t.y = -t.y;
+    return t;
+  }
+  // f + i g packed (both backward transforms are real)
+  template <int M>
+  __device__ __forceinline__ C packed(const C* f, const C* g, int x, const Roots<C>& rt) const {
+    const int mx = x ? M - x : 0;
+    const C fk = __ldg(f + x), gk = __ldg(g + x), fm = __ldg(f + mx), gm = __ldg(g + mx);
+    C P, Q;
+    P.x = fk.x - gk.y;
+    P.y = fk.y + gk.x;
+    Q.x = fm.x + gm.y;
+    Q.y = gm.x - fm.y;
+    C v = cmul(cadd(P, cmul(Q, z4)), tw(x, rt, 1));
+    if (x == 0) {
+      v.x = fk.x;
+      v.y = gk.x;
+    }
+    return v;
+  }
+  template <int M>
+  __device__ __forceinline__ C single(const C* u, int x, const Roots<C>& rt) const {
+    const int mx = x ? M - x : 0;
+    const C p = __ldg(u + x);
+    C q = __ldg(u + mx);
+    q.y = -q.y;
+    C v = cmul(cadd(p, cmul(q, z4)), tw(x, rt, 1));
     if (x == 0) {
       v.x = p.x;
       v.y = 0;
@@ -414,6 +466,57 @@ __device__ __noinline__ void l1_hdot2_residue(const FxArgs* a, int ri, int first
         else h[x] = cadd(p[x], v);
       },
       sync, HDot2Prod{});
+}
+
+// Ternary product of the four-residue form: the first array holds
+// u^f + i u^g, the second u^e (all real); the triple product is real.
+struct Tern4Prod {
+  __device__ __forceinline__ C operator()(C a, C b) const {
+    C p;
+    p.x = a.x * a.y * b.x;
+    p.y = 0;
+    return p;
+  }
+};
+
+// level 1, centered Hermitian ternary convolution of length m = M as four
+// m-point residues (Tern4Terms): residue ri of `count` instances.  The
+// group's two arrays take the packed f + i g and e; both backward
+// transforms, the triple product, one forward transform; the output adds
+// zeta_{4m}^{-rk} S_r(k) / 4m, k < m.  The residue sum is kept in h, or,
+// for in-place calls, in a workspace slot, and h is written at the last
+// residue.
+template <int M>
+__device__ __noinline__ void l1_tern4_residue(const FxArgs* a, int ri, int first, int count, C* sm, Roots<C> rt) {
+  using S = Shape<M>;
+  constexpr int E = S::E, T = S::T, PL = padded(M), GS = group_stride(M, T), TN = 4 * M;
+  const int gi = threadIdx.x / T, i = threadIdx.x % T;
+  const bool act = gi < count;
+  const int64_t off = act ? a->off[a->order[first + gi]] : 0;
+  const C* f = (const C*)a->f + off;
+  const C* g = (const C*)a->g + off;
+  const C* e = (const C*)a->e + off;
+  C* h = (C*)a->h + off;
+  C* p = a->in_place ? (C*)a->tmp + (act ? a->l1tmp[a->order[first + gi]] : 0) : h;
+  C* A = sm + gi * GS;
+  const Real sc = (Real)1 / (Real)(4 * M);
+  const GroupSync<T> sync{1 + gi};
+  const Tern4Terms tt(ri);
+  conv_residue<M, E, TN>(
+      i, true, A, A + PL, rt,
+      [&](int x, int arr, int) {
+        C v = arr ? tt.single<M>(e, x, rt) : tt.packed<M>(f, g, x, rt);
+        if (!act) v.x = v.y = 0;
+        return v;
+      },
+      [&](int x, int, C v) {
+        if (!act) return;
+        v = cscale(tt.out(v, x, rt), sc);
+        if (ri == 0) p[x] = v;
+        else if (ri < 3) p[x] = cadd(p[x], v);
+        else h[x] = cadd(p[x], v);
+      },
+      sync, Tern4Prod{});
 }
 
 // pass A: column tile `tile` of level-2 instance l.  Each pass is its own
@@ -793,14 +896,20 @@ __device__ __noinline__ void run_size(const FxArgs* a, int type, int x, int y, i
         l1_hdot2_residue<M>(a, ri, x, y, sm, rt);
         __syncthreads();
       }
+    } else if constexpr (MODE == MODE_TERN4) {
+#pragma unroll 1
+      for (int ri = 0; ri < 4; ++ri) {
+        l1_tern4_residue<M>(a, ri, x, y, sm, rt);
+        __syncthreads();
+      }
     } else {
       // ternary plans hold two-level sizes only (the planner refuses others)
       if (threadIdx.x == 0) record_error(a->hdr, DC_ERR_DEVICE, M);
     }
   } else {
-    if constexpr (MODE == MODE_PAIR || MODE == MODE_HDOT2) {
-      // gradient-pair and dot-product plans hold one-level sizes only (the
-      // planner refuses others)
+    if constexpr (MODE == MODE_PAIR || MODE == MODE_HDOT2 || MODE == MODE_TERN4) {
+      // gradient-pair, dot-product and four-residue ternary plans hold
+      // one-level sizes only (the planner refuses others)
       if (threadIdx.x == 0) record_error(a->hdr, DC_ERR_DEVICE, M);
     } else {
       // `units` consecutive tiles or row groups; a barrier between them
@@ -900,7 +1009,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) fx_kernel(const __grid
     const long long t_got = clock64();
     if (code != cur) {
       // lo = zeta_TN^b (b < 2^sh), hi = zeta_TN^(a 2^sh), from the full table
-      const int TN = (mode_tables_3m(MODE) ? 3 : 2) * size_of_code(code % kCodeStride);
+      const int TN = mode_q(MODE) * size_of_code(code % kCodeStride);
       const int sh = roots_sh(TN), nlo = 1 << sh, cnt = roots_count(TN);
       const C* tab = (const C*)a.tab[code];
       // the low table always starts shared memory; the high one follows it,
@@ -976,11 +1085,13 @@ dc_status prepare_mode1(int smem, int* blocks);
 dc_status prepare_mode2(int smem, int* blocks);
 dc_status prepare_mode3(int smem, int* blocks);
 dc_status prepare_mode4(int smem, int* blocks);
+dc_status prepare_mode5(int smem, int* blocks);
 dc_status launch_mode0(const FxArgs& a, int grid, int smem, cudaStream_t s);
 dc_status launch_mode1(const FxArgs& a, int grid, int smem, cudaStream_t s);
 dc_status launch_mode2(const FxArgs& a, int grid, int smem, cudaStream_t s);
 dc_status launch_mode3(const FxArgs& a, int grid, int smem, cudaStream_t s);
 dc_status launch_mode4(const FxArgs& a, int grid, int smem, cudaStream_t s);
+dc_status launch_mode5(const FxArgs& a, int grid, int smem, cudaStream_t s);
 
 #if defined(DC_FX_MODE)
 #define DC_FX_CAT2(a, b) a##b
@@ -1116,7 +1227,8 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
   for (int32_t i = 0; i < n; ++i) {
     int c = size_code(m[i]);
     if (c < 0) return false;
-    if ((mode == MODE_TERN && tb.lvl[c] == 1) || ((mode == MODE_PAIR || mode == MODE_HDOT2) && tb.lvl[c] == 2))
+    if ((mode == MODE_TERN && tb.lvl[c] == 1) ||
+        ((mode == MODE_PAIR || mode == MODE_HDOT2 || mode == MODE_TERN4) && tb.lvl[c] == 2))
       return false;
     // the kernel code: variant 1 of the split where the schedule asks for it
     if (((sc.variants >> c) & 1u) && code_ok(c + kCodeStride, mode)) c += kCodeStride;
@@ -1254,7 +1366,7 @@ bool build_plan(const int64_t* m, int32_t n, const int64_t* off, const Schedule&
 
 dc_status prepare_kernel(int smem, int* blocks_per_sm) {
   int bmin = 1 << 20;
-  for (auto prep : {prepare_mode0, prepare_mode1, prepare_mode2, prepare_mode3, prepare_mode4}) {
+  for (auto prep : {prepare_mode0, prepare_mode1, prepare_mode2, prepare_mode3, prepare_mode4, prepare_mode5}) {
     int b = 0;
     const dc_status st = prep(smem, &b);
     if (st != DC_OK) return st;
@@ -1272,6 +1384,7 @@ dc_status launch(const FxArgs& a, int grid, int smem, cudaStream_t s) {
     case MODE_TERN: return launch_mode2(a, grid, smem, s);
     case MODE_PAIR: return launch_mode3(a, grid, smem, s);
     case MODE_HDOT2: return launch_mode4(a, grid, smem, s);
+    case MODE_TERN4: return launch_mode5(a, grid, smem, s);
     default: return DC_ERR_ARG;
   }
 }

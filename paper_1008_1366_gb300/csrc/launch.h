@@ -40,6 +40,10 @@ dc_status fx_pair_run(struct dc_batched_plan* p, const void* w, const void* f, c
 // plan: h = f1 * g1 + f2 * g2; h may be an input
 dc_status fx_hdot2_run(struct dc_batched_plan* p, const void* f1, const void* g1, const void* f2, const void* g2,
                        void* h, void* work, size_t work_bytes, cudaStream_t s);
+// the rows of a centered Hermitian ternary convolution on a MODE_TERN4 plan
+// (one-level m, four m-point residues): h = f * g * e; h may be an input
+dc_status fx_tern4_run(struct dc_batched_plan* p, const void* f, const void* g, const void* e, void* h,
+                       void* work, size_t work_bytes, cudaStream_t s);
 // n centered Hermitian ternary convolutions of length m at stride m on the
 // fixed engine (2m a two-level size of the set): one 1D call, or the rows of
 // a multi-D call; outputs may be inputs

@@ -175,9 +175,22 @@ dc_status plan_md(int pk, int ndim, const int64_t* dims, int ds, bool with_table
   md->rows_mode = row_mode(md->row_kind);
   md->rows_fx = fx_uniform_ok(mlast, ds) && md->rows_mode >= 0 &&
                 ((md->rows_mode != fx::MODE_PAIR && md->rows_mode != fx::MODE_HDOT2) || !fx_uniform_two_level(mlast));
-  // ternary rows whose 2m-point sub-transforms are a two-level size of the
-  // set run on the fixed engine's ternary passes
-  if (md->tern && fx_ternary_ok(mlast, ds)) {
+  // ternary rows of a one-level size of the set run on the fixed engine as
+  // four m-point residues; those whose 2m-point sub-transforms are a
+  // two-level size, on its two-residue ternary passes
+  if (md->tern && fx_uniform_ok(mlast, ds) && !fx_uniform_two_level(mlast)) {
+    md->rows_fx = true;
+    md->rows_mode = fx::MODE_TERN4;
+    rows_bytes = std::max(fx_uniform_work(md->rows_n[0], mlast, ds, md->rows_mode),
+                          fx_uniform_work(md->rows_n[1], mlast, ds, md->rows_mode));
+    if (with_tables) {
+      for (int k = 0; k < 2; ++k) {
+        dc_batched_plan* p = nullptr;
+        dc_status st = fx_uniform_plan(md->rows_n[k], mlast, ds, &p, md->rows_mode);
+        if (st != DC_OK) return st;
+      }
+    }
+  } else if (md->tern && fx_ternary_ok(mlast, ds)) {
     md->rows_fx = true;
     md->rows_mode = fx::MODE_TERN;
     rows_bytes = std::max(fx_ternary_work(mlast, ds, md->rows_n[0]), fx_ternary_work(mlast, ds, md->rows_n[1]));
@@ -217,6 +230,7 @@ dc_status run_rows(const Md& md, const void* const* in, void* const* out, int64_
     if (st != DC_OK) return st;
     if (md.rows_mode == fx::MODE_PAIR) return fx_pair_run(p, in[0], in[1], in[2], out[0], out[1], rw, rb, s);
     if (md.rows_mode == fx::MODE_HDOT2) return fx_hdot2_run(p, in[0], in[1], in[2], in[3], out[0], rw, rb, s);
+    if (md.rows_mode == fx::MODE_TERN4) return fx_tern4_run(p, in[0], in[1], in[2], out[0], rw, rb, s);
     return dc_conv_complex_1d_batched(p, in[0], in[1], out[0], rw, rb, s);
   }
   ConvArgs a{};

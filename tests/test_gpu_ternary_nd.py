@@ -51,9 +51,12 @@ def test_ternary_2d(dc, ms, dtype):
 
 
 # (64, 64, 8), (64, 128, 6): four m-point residues on both outer axes,
-# the second in chunks of 37 slabs (the last one partial)
+# the second in chunks of 37 slabs (the last one partial); (8, 8, 64),
+# (64, 64, 64): rows of a one-level size of the set on the fixed engine's
+# four-residue ternary kind (in 2D: (64, 64), (128, 96), 4096 x 4096)
 @pytest.mark.parametrize("ms,spc", [((2, 2, 2), None), ((3, 4, 5), None), ((4, 4, 4), 3), ((5, 3, 8), 7),
-                                    ((8, 8, 16), None), ((64, 64, 8), None), ((64, 128, 6), 37)])
+                                    ((8, 8, 16), None), ((64, 64, 8), None), ((64, 128, 6), 37),
+                                    ((8, 8, 64), None), ((64, 64, 64), 50)])
 @pytest.mark.parametrize("dtype", DT)
 def test_ternary_3d(dc, ms, spc, dtype):
     f, g, e = inputs(ms, 84, 11 / 6)
