@@ -7,6 +7,11 @@
 //   centered (q = 3): axis holds 2m-1 values, origin at m-1; residue
 //            r = -1, 0, 1 input w_{k,r} of Eqs. (2.4)-(2.5); forward Eq. (2.6)
 //            for k = -m+1..m-1.
+//   ternary  (q = 4, N = 4m of Sec. 4.1 as four m-point residues): axis as
+//            the centered one, U_{-m} = 0; residue r = 0..3 input
+//            zeta_{4m}^{rk} (U_k + zeta_4^{-r} U_{k-m}) (U_0 at k = 0);
+//            forward: S_r(kk) zeta_{4m}^{-r kk} at k = kk and that times
+//            i^r at k = kk - m, summed over r and scaled by 1/(4m).
 // A block of NT threads (256; 512 for complex axes of 2048 points and more)
 // owns one outer index and a tile of W consecutive inner indices (columns);
 // W = NT E / m, T = m / E threads per column.
