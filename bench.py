@@ -487,29 +487,37 @@ def run_suite(args, only=None, peak=None):
     return out
 
 
-def run_per_size(args):
-    """One-size batches of about 16 M elements (FP32, default queue order):
-    time per launch and ps per element, one JSON line per size.  Separates a
-    size's own cost from the cost of mixing sizes in one launch."""
+def per_size_rates(sizes, reps, warm, variants=None, elems=1 << 24):
+    """One-size batches of about `elems` elements (FP32, default queue order,
+    no autotuning): time per launch and ps per element, one record per size.
+    Separates a size's own cost from the cost of mixing sizes in one launch."""
     import torch
     import paper_1008_1366_gb300 as dcl
-    from paper_1008_1366_gb300 import synthetic
     dev = torch.device("cuda", torch.cuda.current_device())
-    sizes = synthetic.SIZES_31 if args.per_size == "all" else [int(x) for x in args.per_size.split(",")]
+    out_recs = []
     for m in sizes:
-        n = max(1, (1 << 24) // m)
+        n = max(1, elems // m)
         f = torch.rand(n * m, dtype=torch.complex64, device=dev)
         g = torch.rand(n * m, dtype=torch.complex64, device=dev)
         plan = dcl.BatchedPlan([m] * n, dtype=torch.complex64)
-        if args.variants:
-            plan.set_variants(int(args.variants, 0))
+        if variants:
+            plan.set_variants(int(variants, 0))
         out = torch.empty_like(f)
         work = plan.workspace(dev)
-        ms, ts = _time_call(lambda: plan(f, g, out=out, work=work), max(3, args.steps), warm=max(3, args.warmup))
+        ms, ts = _time_call(lambda: plan(f, g, out=out, work=work), reps, warm=warm)
         d = plan.describe()[0]
-        print(json.dumps({"m": m, "instances": n, "ms_median": ms, "ps_per_element": ms * 1e9 / (n * m),
-                          "level": d[1], "split": "%dx%d" % (d[3], d[4]) if d[1] == 2 else None}), flush=True)
+        out_recs.append({"m": m, "instances": n, "ms_median": ms, "ps_per_element": ms * 1e9 / (n * m),
+                         "level": d[1], "split": "%dx%d" % (d[3], d[4]) if d[1] == 2 else None})
         del f, g, out, work, plan
+    return out_recs
+
+
+def run_per_size(args):
+    """`--per-size`: one JSON line per size (per_size_rates)."""
+    from paper_1008_1366_gb300 import synthetic
+    sizes = synthetic.SIZES_31 if args.per_size == "all" else [int(x) for x in args.per_size.split(",")]
+    for rec in per_size_rates(sizes, max(3, args.steps), max(3, args.warmup), args.variants):
+        print(json.dumps(rec), flush=True)
 
 
 def cufft_padded_context(ms, tf, tg, stream, reps=5):
@@ -759,9 +767,17 @@ def main():
                             "sample": sample_all}
 
     suite = None
+    per_size = None
     if not args.no_suite and rank == 0 and world == 1:
         del hf, hg, hout
         suite = run_suite(args)
+        # each size of the set alone (about 16 M elements, default plan):
+        # ps per element against the HBM floor of 24 B per element
+        from paper_1008_1366_gb300 import synthetic as _syn
+        recs = per_size_rates(_syn.SIZES_31, reps=5, warm=3)
+        per_size = {"ps_per_element": {str(r["m"]): round(r["ps_per_element"], 2) for r in recs},
+                    "hbm_floor_ps_per_element": round(24.0 / measured_peak_hbm()[0] * 1e3, 2),
+                    "what": "one size per launch, about 16.8 M elements, default plan (no autotuning)"}
 
     alg_bytes = 3 * total * 8
     avg_ms = statistics.mean(per)
@@ -801,6 +817,7 @@ def main():
             "cufft_padded_context": cufft,
             "trace": trace,
             "suite": suite,
+            "per_size": per_size,
         }
         print(json.dumps(line), flush=True)
     if pg:
